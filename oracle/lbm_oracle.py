@@ -1,0 +1,528 @@
+"""Plain FP64 NumPy oracle of one stream-and-collide step of the multicomponent
+lattice Boltzmann model of Sawant, Dorschner & Karlin (arXiv 2004.11286).
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py``; never by the product path.  It is
+deliberately slow and literal: every function follows one passage of the
+paper, in the paper's order and notation, vectorised over grid nodes with
+NumPy and nothing else (no blocking, fusion or reordering).
+
+State layout (an interface convention shared with the C-ABI, not code):
+``pops[L, i, z, y, x]`` with lattices ``L = 0..M-1`` the species populations
+(the transformed ``k_ai`` of Sec. 2.5.2, renamed ``f_ai`` in Sec. 2.5.3),
+``L = M`` the momentum lattice ``f`` and ``L = M+1`` the energy lattice ``g``.
+Velocity index ``i = (cx+1) + 3(cy+1) + 9(cz+1)`` enumerates the D3Q27 set
+of Eq. (d3q27vel); the rest velocity is ``i = 13`` and ``opp(i) = 26 - i``.
+The populations are the post-streaming values at time t.  Lattice units
+``dt = dx = 1`` throughout.
+
+Readings taken where the paper is silent or singular (each also recorded in
+the design notes):
+  * the self-diffusivity D_aa (needed by the b = a terms of Eqs. tau and
+    fStar) defaults to the geometric mean of row a's off-diagonal entries;
+  * the isotropic derivative of Sec. 4.1 is the D3Q27 weighted central
+    stencil d_a phi(x) = 3 sum_i w_i c_ia phi(x + c_i), periodic wrap;
+  * all non-local inputs (grad Y_a, X_alpha) are moments of time t
+    (synchronous evaluation);
+  * strong coupling slaves species ``slaved`` (Eqs. rhoMATCH, uMATCH); its
+    populations are still stored, streamed and relaxed with the slaved
+    density and momentum; the sums of Eqs. rhoMATCH/uMATCH run over all i;
+  * weak coupling: the species equilibria and the Stefan-Maxwell solve use
+    the species' own density and velocity (Eqs. rhoSPEC, uSPEC);
+  * the diffusion velocity of a species whose density is below 1e-14 of
+    the mixture density is taken as zero (it only enters multiplied by
+    rho_a);
+  * at omega == omega_1 exactly, the (omega - omega_1)(g* - g) term of
+    Eq. (g) is replaced by its limit (q_diff and q_corr carry a
+    1/(omega - omega_1) factor).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+Q = 27
+# D3Q27 velocities, Eq. (d3q27vel): c_ia in {-1, 0, 1}.
+C = np.array([[cx, cy, cz] for cz in (-1, 0, 1) for cy in (-1, 0, 1)
+              for cx in (-1, 0, 1)], dtype=np.int64)
+OPP = np.array([int(np.where((C == -C[i]).all(axis=1))[0][0]) for i in range(Q)])
+_C2 = (C * C).sum(axis=1)           # |c_i|^2 in {0, 1, 2, 3}
+
+# Weights of the isotropic gradient stencil (Sec. 4.1 reading): the standard
+# D3Q27 lattice weights, by |c_i|^2.
+_W_ISO = np.array([{0: 8.0 / 27, 1: 2.0 / 27, 2: 1.0 / 54, 3: 1.0 / 216}[int(s)]
+                   for s in _C2])
+
+RHO_EPS = 1e-14
+
+
+@dataclass
+class Params:
+    """Problem statement of Secs. 2-3: species molar masses m_a, molar
+    specific heats (constant, T0 = 0, Sec. 4.1), binary diffusivities D_ab
+    (Eq. smDiffusionCoefficients2), species viscosities and conductivities
+    (Wilke, Eq. viscosityMixture; Mathur, Eq. conductivityMixture) or fixed
+    relaxation rates, and the coupling mode (Sec. 3.5)."""
+    molar_mass: np.ndarray
+    cv_molar: np.ndarray            # C-bar_{a,v} / R_U
+    D: np.ndarray                   # (M, M), symmetric; diag <= 0 -> default
+    mu: Optional[np.ndarray] = None
+    lam: Optional[np.ndarray] = None
+    omega_fixed: float = 0.0
+    omega1_fixed: float = 0.0
+    R_U: float = 1.0
+    coupling: str = "strong"
+    slaved: int = -1
+    M: int = field(init=False)
+
+    def __post_init__(self):
+        self.molar_mass = np.asarray(self.molar_mass, dtype=np.float64)
+        self.cv_molar = np.asarray(self.cv_molar, dtype=np.float64)
+        self.M = int(self.molar_mass.shape[0])
+        D = np.array(self.D, dtype=np.float64).reshape(self.M, self.M)
+        assert np.allclose(D, D.T), "D_ab must be symmetric"
+        for a in range(self.M):
+            if D[a, a] <= 0.0:
+                off = [D[a, b] for b in range(self.M) if b != a]
+                if not off:
+                    raise ValueError("M = 1 needs an explicit D_11 > 0")
+                D[a, a] = float(np.exp(np.mean(np.log(off))))
+        self.D = D
+        if self.mu is not None:
+            self.mu = np.asarray(self.mu, dtype=np.float64)
+        if self.lam is not None:
+            self.lam = np.asarray(self.lam, dtype=np.float64)
+        if self.slaved < 0:
+            self.slaved = self.M - 1
+        assert self.coupling in ("strong", "weak")
+
+    @property
+    def S(self) -> int:
+        return self.M + 2
+
+    @property
+    def R_a(self) -> np.ndarray:
+        """Species gas constants, Eq. (Ra)."""
+        return self.R_U / self.molar_mass
+
+    @property
+    def Cv_a(self) -> np.ndarray:
+        """Mass-based C_{a,v} = C-bar_{a,v} / m_a (Sec. 3.1)."""
+        return self.cv_molar * self.R_U / self.molar_mass
+
+    @property
+    def Cp_a(self) -> np.ndarray:
+        """Mayer's relation in the mass basis, C_{a,p} - C_{a,v} = R_a (Sec. 3.1)."""
+        return self.Cv_a + self.R_a
+
+
+# ----------------------------------------------------------------------------
+# Product-form and energy-lattice ansatz (Secs. 2.4 and 3.4.1)
+# ----------------------------------------------------------------------------
+
+def _psi_1d(c: int, xi, zeta):
+    """The triplet Psi_0, Psi_{+1}, Psi_{-1} of Sec. 2.4."""
+    if c == 0:
+        return 1.0 - (xi * xi + zeta)
+    return (c * xi + (xi * xi + zeta)) / 2.0
+
+
+def psi_product(xi, zeta):
+    """Eq. (prod): Psi_i(xi, zeta) = prod_alpha Psi_{c_ia}(xi_alpha, zeta).
+    ``xi`` has shape (3, ...), ``zeta`` shape (...). Returns (27, ...)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    zeta = np.asarray(zeta, dtype=np.float64)
+    out = np.empty((Q,) + zeta.shape)
+    for i in range(Q):
+        out[i] = (_psi_1d(C[i, 0], xi[0], zeta) * _psi_1d(C[i, 1], xi[1], zeta)
+                  * _psi_1d(C[i, 2], xi[2], zeta))
+    return out
+
+
+def _w_1d(c: int, theta):
+    """Eq. (w0): w_0 = 1 - theta, w_{+-1} = theta / 2."""
+    return 1.0 - theta if c == 0 else theta / 2.0
+
+
+def g_ansatz(theta, M0, m, Mt):
+    """Eqs. (gansatz), (grad), (weights), (RcorrectionPrime), (Bi):
+    G_i = h_i + B_i . Z with product weights w_i(theta).
+    Shapes: theta, M0 (...); m (3, ...); Mt (3, 3, ...). Returns (27, ...)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    M0 = np.asarray(M0, dtype=np.float64)
+    out = np.empty((Q,) + theta.shape)
+    Z = [(1.0 - 3.0 * theta) / (2.0 * theta) * (Mt[a, a] - theta * M0) for a in range(3)]
+    for i in range(Q):
+        c = C[i]
+        w = _w_1d(c[0], theta) * _w_1d(c[1], theta) * _w_1d(c[2], theta)
+        mc = m[0] * c[0] + m[1] * c[1] + m[2] * c[2]
+        second = np.zeros_like(theta)
+        for a in range(3):
+            for b in range(3):
+                delta = 1.0 if a == b else 0.0
+                second = second + (Mt[a, b] - M0 * theta * delta) * (c[a] * c[b] - theta * delta)
+        h = w * (M0 + mc / theta + second / (2.0 * theta * theta))
+        if _C2[i] == 0:
+            B = (1.0, 1.0, 1.0)
+        elif _C2[i] == 1:
+            B = tuple(-0.5 * abs(int(c[a])) for a in range(3))
+        else:
+            B = (0.0, 0.0, 0.0)
+        out[i] = h + B[0] * Z[0] + B[1] * Z[1] + B[2] * Z[2]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Lattice operators
+# ----------------------------------------------------------------------------
+
+def _shift(phi, c):
+    """phi(x + c) on the periodic grid; phi has shape (..., nz, ny, nx)."""
+    return np.roll(phi, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(-3, -2, -1))
+
+
+def iso_derivative(phi, alpha: int):
+    """Second-order isotropic lattice derivative of Sec. 4.1 (reading):
+    d_alpha phi(x) = 3 sum_i w_i c_{i alpha} phi(x + c_i)."""
+    acc = np.zeros_like(phi, dtype=np.float64)
+    for i in range(Q):
+        if C[i, alpha] != 0:
+            acc = acc + _W_ISO[i] * C[i, alpha] * _shift(phi, C[i])
+    return 3.0 * acc
+
+
+def stream(post):
+    """Propagation along the links: the value at x in direction i moves to
+    x + c_i (left-hand sides of Eqs. SMlbm, f, g). ``post`` (S, 27, nz, ny, nx)."""
+    out = np.empty_like(post)
+    for i in range(Q):
+        out[:, i] = np.roll(post[:, i], shift=(int(C[i, 2]), int(C[i, 1]), int(C[i, 0])),
+                            axis=(-3, -2, -1))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Moments, coupling, thermodynamics and transport
+# ----------------------------------------------------------------------------
+
+def moments(pops, prm: Params):
+    """Raw moments: species density and momentum (Eqs. densitya, auxua),
+    mixture density, momentum and pressure tensor of the momentum lattice
+    (Eqs. f0momDensity, f1momMomentum, boldP), total energy and energy flux
+    of the energy lattice (Eqs. g0momTotalEnergy, q)."""
+    M = prm.M
+    Cf = C.astype(np.float64)
+    k, f, g = pops[:M], pops[M], pops[M + 1]
+    out = {}
+    out["rho_a"] = k.sum(axis=1)
+    out["j_a"] = np.einsum("ai...,id->ad...", k, Cf)
+    out["rho"] = f.sum(axis=0)
+    out["j"] = np.einsum("i...,id->d...", f, Cf)
+    out["Pi"] = np.einsum("i...,id,ie->de...", f, Cf, Cf)
+    out["rhoE"] = g.sum(axis=0)
+    out["q"] = np.einsum("i...,id->d...", g, Cf)
+    return out
+
+
+def node_state(mom, prm: Params):
+    """Per-node closure: coupling (Sec. 3.5), composition and equation of state
+    (Sec. 2.1), caloric relations with constant specific heats and T0 = 0
+    (Sec. 3.1, Eq. temperature2, Sec. 4.1), transport (Wilke, Mathur) and the
+    relaxation rates (Eqs. omega, omega1)."""
+    M = prm.M
+    st = dict(mom)
+    rho_a = mom["rho_a"].copy()
+    j_a = mom["j_a"].copy()
+    rho, j = mom["rho"], mom["j"]
+    if prm.coupling == "strong":
+        # Eqs. (rhoMATCH), (uMATCH): the slaved species takes the deficit.
+        s = prm.slaved
+        others = [a for a in range(M) if a != s]
+        rho_a[s] = rho - rho_a[others].sum(axis=0)
+        j_a[s] = j - j_a[others].sum(axis=0)
+        rho_sp = rho
+        u_sp = j / rho
+    else:
+        # Eqs. (rhoSPEC), (uSPEC): the species subsystem's own density/velocity.
+        rho_sp = rho_a.sum(axis=0)
+        u_sp = j_a.sum(axis=0) / rho_sp
+    u = j / rho
+    Y = rho_a / rho_sp                                          # Eq. (mixtureDensity)
+    inv_m = np.einsum("a...,a->...", Y, 1.0 / prm.molar_mass)   # Eq. (meanMolecularWeight)
+    m = 1.0 / inv_m
+    X = Y * (m[None] / prm.molar_mass.reshape((M,) + (1,) * m.ndim))  # Eq. (moleFractionDefinition)
+    R = prm.R_U / m                                             # Eq. (defineSpecificGasContant)
+    Cv = np.einsum("a...,a->...", Y, prm.Cv_a)                 # Eq. (Cvmix)
+    Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
+    usq = (u * u).sum(axis=0)
+    T = (mom["rhoE"] / rho - 0.5 * usq) / Cv                    # Eq. (temperature2), T0 = 0
+    P = rho * R * T                                             # Eq. (eosIdealGas)
+    st.update(rho_a=rho_a, j_a=j_a, rho_sp=rho_sp, u_sp=u_sp, u=u, Y=Y, m=m, X=X,
+              R=R, Cv=Cv, Cp=Cp, T=T, P=P, usq=usq)
+
+    if prm.omega_fixed > 0.0:
+        omega = np.full_like(rho, prm.omega_fixed)
+    else:
+        # Wilke mixture viscosity, Eqs. (viscosityMixture), (wilkePhi).
+        mu_a, ma = prm.mu, prm.molar_mass
+        phi = np.empty((M, M))
+        for a in range(M):
+            for b in range(M):
+                phi[a, b] = ((1.0 + np.sqrt((mu_a[a] / mu_a[b]) * np.sqrt(ma[b] / ma[a]))) ** 2
+                             / (np.sqrt(8.0) * np.sqrt(1.0 + ma[a] / ma[b])))
+        mu_mix = np.zeros_like(rho)
+        for a in range(M):
+            den = np.zeros_like(rho)
+            for b in range(M):
+                den = den + phi[a, b] * X[b]
+            mu_mix = mu_mix + mu_a[a] * X[a] / den
+        omega = 2.0 * P / (P + 2.0 * mu_mix)                    # Eq. (omega), dt = 1
+    if prm.omega1_fixed > 0.0:
+        omega1 = np.full_like(rho, prm.omega1_fixed)
+    else:
+        # Mathur mixture conductivity, Eq. (conductivityMixture).
+        lam_a = prm.lam
+        s1 = np.einsum("a...,a->...", X, lam_a)
+        s2 = np.einsum("a...,a->...", X, 1.0 / lam_a)
+        lam_mix = 0.5 * (s1 + 1.0 / s2)
+        omega1 = 2.0 * P * Cp / (P * Cp + 2.0 * lam_mix)        # Eq. (omega1), dt = 1
+    st.update(omega=omega, omega1=omega1)
+    return st
+
+
+def inv_tau_ab(st, prm: Params):
+    """Eq. (tauab): 1/tau_ab = (R_U T / D_ab) (m / (m_a m_b)), all a, b."""
+    M = prm.M
+    out = np.empty((M, M) + st["T"].shape)
+    for a in range(M):
+        for b in range(M):
+            out[a, b] = (prm.R_U * st["T"] / prm.D[a, b]) * (
+                st["m"] / (prm.molar_mass[a] * prm.molar_mass[b]))
+    return out
+
+
+def sm_momenta(st, prm: Params, itab=None):
+    """Species velocities u_a(f) from Eq. (transform1):
+    rho_a u_a(f) (1 + 1/(2 tau_a)) - (1/2) Y_a sum_b (1/tau_ab) rho_b u_b(f)
+        = rho_a u_a(k),
+    one M x M linear system per node, three right-hand sides (the components).
+    Returns the diffusion velocities V_a = u_a(f) - u (Sec. 2.5.3)."""
+    M = prm.M
+    if itab is None:
+        itab = inv_tau_ab(st, prm)
+    Y = st["Y"]
+    inv_tau_a = np.einsum("ab...,b...->a...", itab, Y)          # Eq. (tau)
+    shape = st["T"].shape
+    n = int(np.prod(shape)) if shape else 1
+    A = np.zeros((n, M, M))
+    for a in range(M):
+        for b in range(M):
+            val = -0.5 * Y[a] * itab[a, b]
+            if a == b:
+                val = val + 1.0 + 0.5 * inv_tau_a[a]
+            A[:, a, b] = val.reshape(n)
+    rhs = st["j_a"].reshape(M, 3, n).transpose(2, 0, 1)         # (n, M, 3)
+    p = np.linalg.solve(A, rhs)                                 # rho_a u_a(f)
+    p = p.transpose(1, 2, 0).reshape((M, 3) + shape)
+    rho_a = st["rho_a"]
+    ok = rho_a > RHO_EPS * st["rho_sp"]
+    safe = np.where(ok, rho_a, 1.0)
+    V = np.where(ok[:, None], p / safe[:, None] - st["u_sp"][None], 0.0)
+    return V
+
+
+# ----------------------------------------------------------------------------
+# Collision
+# ----------------------------------------------------------------------------
+
+def collide(pops, prm: Params, return_aux: bool = False):
+    """Post-collision populations at every node (before propagation) for the
+    species (Eqs. SMlbm, fstar1, transform12), the momentum lattice with the
+    D3Q27 correction (Eqs. feq, fwithcorrection, Xalpha, Ai) and the energy
+    lattice (Eqs. g, gieq, gistar, gstareq1mom, interdiffusion, corrFourier)."""
+    M = prm.M
+    mom = moments(pops, prm)
+    st = node_state(mom, prm)
+    rho, j, u, T, P, R = st["rho"], st["j"], st["u"], st["T"], st["P"], st["R"]
+    omega, omega1 = st["omega"], st["omega1"]
+
+    # --- non-local fields (Sec. 4.1 derivatives of time-t moments) ---------
+    Phi = [j[a] * (1.0 - 3.0 * R * T) - rho * u[a] ** 3 for a in range(3)]
+    c_om = 1.0 / omega - 0.5
+    Gs = [c_om * iso_derivative(Phi[a], a) for a in range(3)]
+    Xc = np.stack([-iso_derivative(Gs[a], a) for a in range(3)])      # Eq. (Xalpha)
+    gradY = np.stack([np.stack([iso_derivative(st["Y"][a], b) for b in range(3)])
+                      for a in range(M)])                              # (M, 3, ...)
+
+    # --- species, Eqs. (tauab), (tau), beta_a, (SMlbm), (fstar1) ------------
+    itab = inv_tau_ab(st, prm)
+    V = sm_momenta(st, prm, itab)
+    inv_tau_a = np.einsum("ab...,b...->a...", itab, st["Y"])
+    beta = 1.0 / (2.0 / inv_tau_a + 1.0)                       # dt / (2 tau_a + dt)
+    feq_s = np.stack([st["rho_a"][a] * psi_product(st["u_sp"], prm.R_a[a] * T)
+                      for a in range(M)])
+    fstar_s = np.stack([st["rho_a"][a] * psi_product(st["u_sp"] + V[a], prm.R_a[a] * T)
+                        for a in range(M)])
+    diff = feq_s - fstar_s
+    post = np.empty_like(pops)
+    for a in range(M):
+        F = np.zeros_like(diff[0])
+        for b in range(M):
+            F = F + itab[a, b] * diff[b]
+        F = st["Y"][a] * F
+        k = pops[a]
+        post[a] = k + 2.0 * beta[a] * (feq_s[a] - k) + (beta[a] - 1.0) * F
+
+    # --- momentum lattice, Eqs. (feq), (fwithcorrection), (Ai) ---------------
+    f = pops[M]
+    feq = rho * psi_product(u, R * T)
+    corr = np.zeros_like(f)
+    for i in range(Q):
+        if _C2[i] == 1:
+            corr[i] = 0.5 * (C[i, 0] * Xc[0] + C[i, 1] * Xc[1] + C[i, 2] * Xc[2])
+    post[M] = f + omega * (feq - f) + corr
+
+    # --- energy lattice, Eqs. (g), (geq1mom), (geq2mom), (gstareq1mom) -------
+    g = pops[M + 1]
+    theta = R * T
+    H_a = np.stack([prm.Cp_a[a] * T for a in range(M)])       # Eq. (specHa), T0 = 0
+    H = st["Cp"] * T                                           # Eq. (specH)
+    eye = np.eye(3)
+    Peq = np.empty((3, 3) + rho.shape)
+    for a in range(3):
+        for b in range(3):
+            Peq[a, b] = P * eye[a, b] + rho * u[a] * u[b]       # Eq. (feq2mom)
+    hk = H + 0.5 * st["usq"]
+    qeq = hk[None] * j                                          # Eq. (geq1mom)
+    Req = np.empty_like(Peq)
+    for a in range(3):
+        for b in range(3):
+            Req[a, b] = hk * Peq[a, b] + P * u[a] * u[b]        # Eq. (geq2mom)
+    geq = g_ansatz(theta, st["rhoE"], qeq, Req)                # Eq. (gieq)
+
+    Pi = st["Pi"]
+    qb = np.stack([st["q"][a] - sum(u[b] * (Pi[b, a] - Peq[b, a]) for b in range(3))
+                   for a in range(3)])
+    sHYV = sum(H_a[a][None] * st["Y"][a][None] * V[a] for a in range(M))
+    sHgY = sum(H_a[a][None] * gradY[a] for a in range(M))
+    dw = omega - omega1
+    nonzero = dw != 0.0
+    dw_safe = np.where(nonzero, dw, 1.0)
+    qdiff = (omega1 / dw_safe)[None] * rho[None] * sHYV        # Eq. (interdiffusion)
+    qcorr = (0.5 * (omega1 - 2.0) / (-dw_safe) * P)[None] * sHgY  # Eq. (corrFourier)
+    qstar = qb + qdiff + qcorr                                  # Eq. (gstareq1mom)
+    gstar = g_ansatz(theta, st["rhoE"], qstar, Req)            # Eq. (gistar)
+    relax_star = dw * (gstar - g)
+    if not nonzero.all():
+        # Limit omega -> omega_1: G is affine in m, so (omega - omega_1)(g* - g)
+        # -> w_i(theta) c_i . [omega_1 rho sum H_a Y_a V_a
+        #                      + (1/2)(2 - omega_1) P sum H_a grad Y_a] / theta.
+        flux = omega1[None] * rho[None] * sHYV + (0.5 * (2.0 - omega1) * P)[None] * sHgY
+        lim = np.empty_like(g)
+        for i in range(Q):
+            c = C[i]
+            w = _w_1d(c[0], theta) * _w_1d(c[1], theta) * _w_1d(c[2], theta)
+            lim[i] = w * (c[0] * flux[0] + c[1] * flux[1] + c[2] * flux[2]) / theta
+        relax_star = np.where(nonzero[None], relax_star, lim)
+    post[M + 1] = g + omega1 * (geq - g) + relax_star
+
+    if return_aux:
+        aux = dict(st)
+        aux.update(V=V, Xc=Xc, gradY=gradY, beta=beta, itab=itab, feq_s=feq_s,
+                   fstar_s=fstar_s, feq=feq, geq=geq, gstar=gstar, qstar=qstar, Peq=Peq,
+                   qeq=qeq, Req=Req, Phi=np.stack(Phi), G=np.stack(Gs))
+        return post, aux
+    return post
+
+
+def step(pops, prm: Params):
+    """One time step: collide at every node, then stream (Eqs. SMlbm, fwithcorrection, g)."""
+    return stream(collide(pops, prm))
+
+
+def run(pops, prm: Params, nsteps: int):
+    for _ in range(nsteps):
+        pops = step(pops, prm)
+    return pops
+
+
+# ----------------------------------------------------------------------------
+# Initialisation and outputs
+# ----------------------------------------------------------------------------
+
+def init_populations(X, u, T, P, prm: Params):
+    """Equilibrium initial state from mole fractions, velocity, temperature
+    and pressure.  Species: f^eq_a = rho_a Psi(u, R_a T) (Eq. 27eq), which by
+    Eq. (fixed) is also the equilibrium of the transformed populations.
+    Momentum lattice: rho Psi(u, RT) (Eq. feq).  Energy lattice: g^eq of
+    Eq. (gieq).  X (M, ...), u (3, ...), T and P (...)."""
+    M = prm.M
+    X = np.asarray(X, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    mm = prm.molar_mass.reshape((M,) + (1,) * T.ndim)
+    m = (X * mm).sum(axis=0)                       # 1/m = sum Y_a/m_a  <=>  m = sum X_a m_a
+    Y = X * mm / m[None]
+    R = prm.R_U / m
+    rho = P / (R * T)
+    rho_a = Y * rho[None]
+    j = rho[None] * u
+    Cv = np.einsum("a...,a->...", Y, prm.Cv_a)
+    Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
+    usq = (u * u).sum(axis=0)
+    rhoE = rho * (Cv * T + 0.5 * usq)
+    pops = np.empty((M + 2, Q) + T.shape)
+    for a in range(M):
+        pops[a] = rho_a[a] * psi_product(u, prm.R_a[a] * T)
+    pops[M] = rho * psi_product(u, R * T)
+    H = Cp * T
+    hk = H + 0.5 * usq
+    eye = np.eye(3)
+    Peq = np.empty((3, 3) + T.shape)
+    Req = np.empty((3, 3) + T.shape)
+    for a in range(3):
+        for b in range(3):
+            Peq[a, b] = P * eye[a, b] + rho * u[a] * u[b]
+    for a in range(3):
+        for b in range(3):
+            Req[a, b] = hk * Peq[a, b] + P * u[a] * u[b]
+    pops[M + 1] = g_ansatz(R * T, rhoE, hk[None] * j, Req)
+    return pops
+
+
+def macroscopic(pops, prm: Params):
+    """Observable fields of the state: rho, u, T, P, X_a, Y_a and the diffusion
+    velocities V_a (the species velocity is u + V_a, Sec. 2.5.3)."""
+    st = node_state(moments(pops, prm), prm)
+    V = sm_momenta(st, prm)
+    return dict(rho=st["rho"], u=st["u"], T=st["T"], P=st["P"], X=st["X"], Y=st["Y"], V=V,
+                omega=st["omega"], omega1=st["omega1"])
+
+
+def collide_patch_center(pops, z: int, y: int, x: int, prm: Params, radius: int = 2):
+    """Post-collision populations of the single node (z, y, x) of a periodic
+    grid, computed by ``collide`` on the (2r+1)^3 periodic neighbourhood.  The
+    non-local terms reach two nodes away (X_alpha differentiates twice), so
+    r = 2 reproduces the full-grid result exactly at the centre."""
+    nz, ny, nx = pops.shape[-3:]
+    iz = (np.arange(z - radius, z + radius + 1)) % nz
+    iy = (np.arange(y - radius, y + radius + 1)) % ny
+    ix = (np.arange(x - radius, x + radius + 1)) % nx
+    patch = pops[:, :, iz][:, :, :, iy][:, :, :, :, ix]
+    post = collide(np.ascontiguousarray(patch), prm)
+    return post[:, :, radius, radius, radius]
+
+
+def conserved_sums(pops, prm: Params):
+    """Grid sums of every stored lattice's density, the mixture momentum and
+    the total energy: [sum rho_a (a = 1..M), sum rho, sum j (3), sum rhoE]."""
+    mom = moments(pops, prm)
+    out = [mom["rho_a"][a].sum() for a in range(prm.M)]
+    out.append(mom["rho"].sum())
+    out.extend(mom["j"][d].sum() for d in range(3))
+    out.append(mom["rhoE"].sum())
+    return np.array(out)

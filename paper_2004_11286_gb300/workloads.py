@@ -1,0 +1,202 @@
+"""Seeded synthetic workloads shaped like the paper's benchmarks (Sec. 4).
+
+This module only draws and lays out INPUTS: species constants, transport
+inputs and the initial macroscopic fields (mole fractions, velocity,
+temperature, pressure) as float64 NumPy arrays.  It contains none of the
+method's arithmetic (no equilibria, no moments, no collision), so both the
+CUDA path and the CPU oracle can be fed from it.
+
+Recipes (stand-ins for the paper's experiments; lattice units, R_U = 1):
+  * ``ternary_tube``   -- periodic analogue of the Loschmidt tube of Sec. 4.2
+    (64x4x4, m = 2, 40, 16, D12 = D13 = 0.05, D23 = 0.01, left/right mole
+    fractions (0.5, 0.5, 0) / (0.5, 0, 0.5) joined by tanh steps of width 2).
+  * ``acoustic_pulse`` -- binary sound-speed test after Sec. 4.4 (128^3,
+    m = 4, 40, uniform X_1, Gaussian pressure pulse of amplitude 1e-3 and
+    standard deviation 6 cells at the centre).
+  * ``shear_layer``    -- periodic double shear layer after Sec. 4.5 (256^3,
+    m = 2, 28, tanh velocity and composition profiles of thickness 4,
+    U0 = 0.3 c_s, seeded white noise 1e-3 U0 on u_y).
+  * ``random_mixture`` -- smooth random M-species field (sum of 16 Fourier
+    modes per species), random molar masses and diffusivities.
+Common choices: T = 0.5; reference pressure P0 = T / m_mean with m_mean the
+molar mass of the domain-mean composition (reference density 1);
+mu_a = 0.1 P0 (0.025 P0 for the shear layer), lambda_a = mu_a c_pa / 0.71
+with c_pa = (cv_a + 1) R_U / m_a; cv_a = C-bar_{a,v}/R_U chosen by molar mass
+(monatomic 3/2, diatomic 5/2, polyatomic 3).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Dict, Optional
+
+import numpy as np
+
+T_AMBIENT = 0.5
+PR_TARGET = 0.71
+
+_CV_BY_MASS = {2.0: 2.5, 4.0: 1.5, 16.0: 3.0, 28.0: 2.5, 40.0: 1.5, 44.0: 3.0}
+
+
+def cv_for_mass(m: float) -> float:
+    """Molar C_v / R_U by molecular identity of the molar mass."""
+    return _CV_BY_MASS.get(float(m), 2.5)
+
+
+@dataclass
+class Workload:
+    name: str
+    molar_mass: np.ndarray        # (M,)
+    cv_molar: np.ndarray          # (M,)
+    D: np.ndarray                 # (M, M), diagonal 0 -> library default rule
+    mu: np.ndarray                # (M,)
+    lam: np.ndarray               # (M,)
+    X: np.ndarray                 # (M, nz, ny, nx)
+    u: np.ndarray                 # (3, nz, ny, nx)
+    T: np.ndarray                 # (nz, ny, nx)
+    P: np.ndarray                 # (nz, ny, nx)
+    steps: int
+    R_U: float = 1.0
+
+    @property
+    def M(self) -> int:
+        return int(self.molar_mass.shape[0])
+
+    @property
+    def shape(self):
+        return tuple(self.T.shape)
+
+    @property
+    def nodes(self) -> int:
+        return int(np.prod(self.T.shape))
+
+    def params(self, **overrides) -> Dict:
+        d = dict(molar_mass=self.molar_mass.copy(), cv_molar=self.cv_molar.copy(),
+                 D=self.D.copy(), mu=self.mu.copy(), lam=self.lam.copy(), R_U=self.R_U)
+        d.update(overrides)
+        return d
+
+
+def _transport(molar_mass, cv_molar, P0, mu_factor):
+    M = len(molar_mass)
+    mu = np.full(M, mu_factor * P0)
+    cp = (cv_molar + 1.0) / molar_mass
+    lam = mu * cp / PR_TARGET
+    return mu, lam
+
+
+def _p0(X_mean, molar_mass, T):
+    m_mean = float(np.dot(X_mean, molar_mass))
+    return T / m_mean
+
+
+def ternary_tube(nx: int = 64, ny: int = 4, nz: int = 4, steps: int = 1000) -> Workload:
+    mm = np.array([2.0, 40.0, 16.0])
+    cv = np.array([cv_for_mass(m) for m in mm])
+    D = np.array([[0.0, 0.05, 0.05], [0.05, 0.0, 0.01], [0.05, 0.01, 0.0]])
+    XL = np.array([0.5, 0.5, 0.0])
+    XR = np.array([0.5, 0.0, 0.5])
+    x = np.arange(nx, dtype=np.float64)
+    h = nx / 2.0
+    # periodic double tanh step: right state on [h, nx), left on [0, h)
+    s = 0.5 * (np.tanh((x - (h - 0.5)) / 2.0) - np.tanh((x - (nx - 0.5)) / 2.0)
+               - np.tanh((x + 0.5) / 2.0) + 1.0)
+    X = (1.0 - s)[None] * XL[:, None] + s[None] * XR[:, None]
+    X = np.broadcast_to(X[:, None, None, :], (3, nz, ny, nx)).copy()
+    X = X / X.sum(axis=0, keepdims=True)
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(X.reshape(3, -1).mean(axis=1), mm, T_AMBIENT)
+    P = np.full((nz, ny, nx), P0)
+    u = np.zeros((3, nz, ny, nx))
+    mu, lam = _transport(mm, cv, P0, 0.1)
+    return Workload("ternary_tube", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
+def acoustic_pulse(n: int = 128, x1: float = 0.5, amplitude: float = 1e-3, sigma: float = 6.0,
+                   steps: int = 2000, shape: Optional[tuple] = None) -> Workload:
+    mm = np.array([4.0, 40.0])
+    cv = np.array([cv_for_mass(m) for m in mm])
+    D = np.array([[0.0, 0.05], [0.05, 0.0]])
+    nz, ny, nx = shape if shape is not None else (n, n, n)
+    X = np.empty((2, nz, ny, nx))
+    X[0] = x1
+    X[1] = 1.0 - x1
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(np.array([x1, 1.0 - x1]), mm, T_AMBIENT)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r2 = (x - nx / 2.0) ** 2 + (y - ny / 2.0) ** 2 + (z - nz / 2.0) ** 2
+    P = P0 * (1.0 + amplitude * np.exp(-r2 / (2.0 * sigma ** 2)))
+    u = np.zeros((3, nz, ny, nx))
+    mu, lam = _transport(mm, cv, P0, 0.1)
+    return Workload("acoustic_pulse", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
+def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: float = 1e-3,
+                seed: int = 1234, steps: int = 5000, shape: Optional[tuple] = None) -> Workload:
+    mm = np.array([2.0, 28.0])
+    cv = np.array([cv_for_mass(m) for m in mm])
+    D = np.array([[0.0, 0.05], [0.05, 0.0]])
+    nz, ny, nx = shape if shape is not None else (n, n, n)
+    y = np.arange(ny, dtype=np.float64)
+    y1, y2 = ny / 4.0, 3.0 * ny / 4.0
+    band = 0.5 * (np.tanh((y - y1) / delta) - np.tanh((y - y2) / delta))   # 1 inside the band
+    XA = band
+    X = np.empty((2, nz, ny, nx))
+    X[0] = XA[None, :, None]
+    X[1] = 1.0 - X[0]
+    # reference sound speed of the 50/50 mixture (input recipe, Sec. 4.1 scaling)
+    m50 = 0.5 * (mm[0] + mm[1])
+    y50 = 0.5 * mm / m50
+    cv50 = float(np.dot(y50, cv / mm))
+    R50 = 1.0 / m50
+    gamma50 = (cv50 + R50) / cv50
+    U0 = mach * np.sqrt(gamma50 * R50 * T_AMBIENT)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = (U0 * (2.0 * band - 1.0))[None, :, None]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u[1] = noise * U0 * rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(np.array([0.5, 0.5]), mm, T_AMBIENT)
+    P = np.full((nz, ny, nx), P0)
+    mu, lam = _transport(mm, cv, P0, 0.025)
+    return Workload("shear_layer", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
+def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
+                   shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nz, ny, nx = shape if shape is not None else (n, n, n)
+    mm = rng.uniform(2.0, 44.0, size=M)
+    cv = rng.choice(np.array([1.5, 2.5, 3.0]), size=M)
+    D = np.zeros((M, M))
+    for a in range(M):
+        for b in range(a + 1, M):
+            D[a, b] = D[b, a] = float(np.exp(rng.uniform(np.log(0.005), np.log(0.1))))
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    Xt = np.empty((M, nz, ny, nx))
+    for a in range(M):
+        phi = np.zeros((nz, ny, nx))
+        for _ in range(modes):
+            kx, ky, kz = rng.integers(-3, 4, size=3)
+            A = rng.uniform(0.0, 1.0)
+            ps = rng.uniform(0.0, 2.0 * np.pi)
+            phi += A * np.cos(2.0 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ps)
+        mx = np.abs(phi).max()
+        phi = phi / mx if mx > 0 else phi
+        Xt[a] = np.maximum(0.05, 1.0 + 0.5 * phi)
+    X = Xt / Xt.sum(axis=0, keepdims=True)
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(X.reshape(M, -1).mean(axis=1), mm, T_AMBIENT)
+    P = np.full((nz, ny, nx), P0)
+    u = np.zeros((3, nz, ny, nx))
+    if velocity > 0.0:
+        u = velocity * rng.uniform(-1.0, 1.0, size=(3, nz, ny, nx))
+    mu, lam = _transport(mm, cv, P0, 0.1)
+    return Workload("random_mixture", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
+def perturbation(shape, scale: float, seed: int) -> np.ndarray:
+    """Seeded multiplicative noise (1 + scale * U(-1, 1)) used by tests to move
+    a state off equilibrium; drawn here so both sides see the same numbers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return 1.0 + scale * rng.uniform(-1.0, 1.0, size=shape)
