@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the fused multicomponent D3Q27 stream-and-collide step.
+
+Workload (N = 1 GPU): the binary acoustic pulse on a 128^3 periodic grid,
+M = 2 species (molar masses 4, 40), FP32, i.e. 2 species + f + g lattices,
+108 populations per node.  One bench step = one lattice time step of the
+whole grid (all lattices).  The populations (906 MB) are larger than L2, so
+no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
+(the only other implementation of the method) on a bounded periodic sample of
+the same workload on the host cores.  Under torchrun each rank runs an
+independent replica (the single-GPU problem does not shard without a halo
+exchange, which is not built): value = all ranks' lattice updates / max time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (species+f+g) and HBM-roofline fraction, plain FP32 vs chosen form"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--n", type=int, default=128, help="grid edge of the acoustic-pulse workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", nargs=2, type=int, metavar=("EDGE", "STEPS"),
+                    help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample_worker(edge: int, steps: int, warmup: int = 1):
+    import numpy as np
+    import oracle as O
+    from paper_2004_11286_gb300 import workloads as W
+    wl = W.acoustic_pulse(n=edge, sigma=6.0 * edge / 128.0)
+    prm = O.Params(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, slaved=W.slaved_species(wl))
+    pops = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm)
+    for _ in range(warmup):
+        pops = O.step(pops, prm)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pops = O.step(pops, prm)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(pops).all()
+    return dict(nodes=wl.nodes, steps=steps, seconds=dt, mlups=wl.nodes * steps / dt / 1e6)
+
+
+def _run_oracle_subprocess(edge: int, steps: int, timeout: float = 900.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(edge), str(steps)],
+                       capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_baseline(target_seconds: float = 15.0):
+    cal = _run_oracle_subprocess(16, 2)
+    per_node_step = cal["seconds"] / (cal["nodes"] * cal["steps"])
+    edge, steps = 48, max(2, int(target_seconds / (per_node_step * 48 ** 3)))
+    res = _run_oracle_subprocess(edge, steps)
+    return {"value": round(res["mlups"], 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"acoustic pulse recipe on a {edge}^3 periodic grid, {steps} steps, "
+                      f"FP64 NumPy oracle, one thread ({res['seconds']:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.window = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), [v.strip() for v in line.split(",")]))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        t0, t1 = self.window if self.window else (0, float("inf"))
+        inside = [s for (t, s) in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or [s for (_, s) in self.samples]
+        if not inside:
+            return None
+        sm = [float(s[1]) for s in inside if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in inside if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in inside for k in range(4) if len(s) > 5 + k and s[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+def _physical_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if parts and all(p.strip().isdigit() for p in parts) and local_rank < len(parts):
+        return int(parts[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# Roofline bookkeeping
+# ---------------------------------------------------------------------------
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBps", "copy_gbs"):
+            if key in d:
+                return float(d[key]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2004_11286_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str, precision: str, M: int, nodes: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}/{precision}/M{M}")
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None
+    return float(e["bytes_per_node"]) * nodes
+
+
+def _algorithmic_bytes(M: int, precision: str, slaved_skipped: bool = True):
+    """Per-node algorithmic bytes of each kernel and of the whole step."""
+    b = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    bs = 8 if precision == "fp64" else 4
+    S = M + 2
+    read_side = (S - (1 if slaved_skipped else 0)) * 27 * b
+    return {
+        "side_fields": read_side + 5 * bs,          # moments of the non-slaved lattices -> 5 side fields
+        "grad_G": 4 * bs + 3 * bs,                  # Phi, c_omega -> G
+        "collide_stream": 2 * 27 * S * b + 4 * bs,  # every population read + written, G and C_p read
+        "step": 2 * 27 * S * b + 2 * 5 * bs,        # method minimum: populations once + side fields once
+    }
+
+
+# ---------------------------------------------------------------------------
+def main():
+    a = _args()
+    if a.oracle_sample:
+        print(json.dumps(_oracle_sample_worker(*a.oracle_sample)))
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        cal = _run_oracle_subprocess(16, 2)
+        per = cal["seconds"] / (cal["nodes"] * cal["steps"])
+        budget = 150.0 / max(1, a.steps + a.warmup)
+        edge = int(max(8, min(a.n, round((budget / per) ** (1.0 / 3.0)))))
+        res = _run_oracle_subprocess(edge, a.steps, timeout=1800)
+        v = round(res["mlups"], 6)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": round(1e3 * res["seconds"] / a.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"acoustic pulse, M=2 (m=4,40), {edge}^3 periodic sample of the "
+                                       f"{a.n}^3 workload", "precision": "fp64"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{edge}^3 periodic grid, {a.steps} steps"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2004_11286_gb300 import binding, build, workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    binding.load_library()
+
+    wl = W.acoustic_pulse(n=a.n)
+    slaved = W.slaved_species(wl)
+    h = binding.LbmMix(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, shape=wl.shape,
+                       precision=a.precision, slaved=slaved, R_U=wl.R_U, device=dev)
+    stream = h.stream
+    Xd = torch.from_numpy(wl.X.ravel()).to(dev)
+    ud = torch.from_numpy(wl.u.ravel()).to(dev)
+    Td = torch.from_numpy(wl.T.ravel()).to(dev)
+    Pd = torch.from_numpy(wl.P.ravel()).to(dev)
+    h.init_fields(Xd, ud, Td, Pd)
+    h.step(a.warmup)
+    h.synchronize()
+
+    # ---- device-timed region --------------------------------------------
+    clocks = ClockSampler(_physical_gpu_index(local_rank))
+    time.sleep(0.3)
+    h.enable_kernel_timing(True)
+    h.kernel_times()                                   # clear
+    launches0 = h.launch_count
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_host0 = time.perf_counter()
+    ev0.record(stream)
+    h.step(a.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_host1 = time.perf_counter()
+    if world > 1:
+        dist.barrier()
+    clocks.mark(t_host0, t_host1)
+    launches = h.launch_count - launches0
+    kt = h.kernel_times()
+    h.enable_kernel_timing(False)
+    h.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    N = wl.nodes
+    value = world * N * a.steps / (elapsed_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    alg = _algorithmic_bytes(wl.M, a.precision)
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(1, kt[dom][1])
+    peak, peak_src = _peaks()
+    achieved = alg[dom] * N / (dom_ms * 1e-3) / 1e9
+    step_alg_gbs = alg["step"] * N * a.steps / (elapsed_ms * 1e-3) / 1e9
+    traffic = _recorded_traffic(dom, a.precision, wl.M, N)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "peak_source": peak_src + (" (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                                           else " (6.8 TB/s, profiling recipe)"),
+                "algorithmic_bytes_per_node": alg[dom],
+                "kernel_ms_avg": round(dom_ms, 5),
+                "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in kt.values())), 4) for k, v in kt.items()},
+                "step_algorithmic_bytes_per_node": alg["step"],
+                "step_frac": round(step_alg_gbs / peak, 4)}
+
+    # ---- end to end through the public API with host buffers ---------------
+    e2e = None
+    if not a.no_e2e:
+        Xp = torch.from_numpy(wl.X.ravel()).pin_memory()
+        up = torch.from_numpy(wl.u.ravel()).pin_memory()
+        Tp = torch.from_numpy(wl.T.ravel()).pin_memory()
+        Pp = torch.from_numpy(wl.P.ravel()).pin_memory()
+        outp = torch.empty(h.n_outputs * N, dtype=torch.float64).pin_memory()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h.init_fields(Xp, up, Tp, Pp)
+        h.step(a.steps)
+        h.moments(outp)
+        sums = h.diagnostics()
+        t1 = time.perf_counter()
+        e2e_s = t1 - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        assert np.isfinite(sums).all()
+        h2d = (wl.M + 5) * N * 8
+        d2h = h.n_outputs * N * 8 + (wl.M + 5) * 8
+        e2e = {"value": round(world * N * a.steps / e2e_s / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": round(h2d / a.steps, 1), "d2h_bytes_per_step": round(d2h / a.steps, 1),
+               "note": "init_fields from pinned host fields + step(K) + get_moments to pinned host + "
+                       "diagnostics, host wall clock"}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline and world == 1:
+        try:
+            cpu = _cpu_baseline()
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": round(elapsed_ms / a.steps, 5), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision,
+                "data": "synthetic",
+                "config": {"workload": f"binary acoustic pulse, {a.n}^3 periodic D3Q27, M=2 (m=4,40), "
+                                       f"species+f+g = {27 * (wl.M + 2)} populations/node, {a.precision}",
+                           "grid": list(wl.shape), "M": wl.M, "precision": a.precision,
+                           "l2": "inputs larger than L2 (%.0f MB of populations), no flush" %
+                                 (27 * (wl.M + 2) * N * {"fp64": 8, "fp32": 4}.get(a.precision, 2) / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * lbm_mix.h -- C ABI of the GB300 multicomponent lattice Boltzmann library.
+ *
+ * One fused stream-and-collide step of the Stefan-Maxwell + compressible
+ * two-population model of Sawant, Dorschner & Karlin (arXiv 2004.11286) on
+ * the D3Q27 lattice: M species lattices (Sec. 2.5.3, Eqs. SMlbm, fstar1,
+ * transform12), the momentum lattice f with the D3Q27 third-moment
+ * correction (Sec. 3.4.2, Eqs. feq, fwithcorrection, Xalpha, Ai) and the
+ * energy lattice g (Sec. 3.2, Eq. g; Sec. 3.4.1, Eqs. gansatz-gistar),
+ * coupled as in Sec. 3.5 (weak or strong coupling).
+ *
+ * Conventions shared by every call:
+ *   - Units: lattice units, dt = dx = 1, constant specific heats with T0 = 0
+ *     (Sec. 4.1).
+ *   - Node order: x fastest, then y, then z; N = nx*ny*nz nodes.
+ *   - Velocity index: i = (cx+1) + 3*(cy+1) + 9*(cz+1), c in {-1,0,1}^3
+ *     (Eq. d3q27vel); rest velocity i = 13; opposite of i is 26 - i.
+ *   - Lattice index L: 0..M-1 species, M momentum lattice f, M+1 energy
+ *     lattice g; S = M + 2 lattices are stored.
+ *   - Host/device arguments: a `host_ptrs` flag of 1 means the pointer is a
+ *     host address (pinned or pageable); 0 means a device address on the
+ *     handle's device.  Arrays are float64, caller-owned, and are only read
+ *     or written during the call (host copies are synchronous with respect
+ *     to the caller; device-pointer calls are ordered on the handle's
+ *     stream and return before the GPU work completes).
+ *   - Errors: every call returns an lbm_status; lbm_mix_last_error() gives
+ *     a one-line message.  Kernels latch device-side conditions (a node with
+ *     non-positive density or temperature, or a non-finite value) into a flag
+ *     word; the next call that synchronises (lbm_mix_synchronize,
+ *     lbm_mix_diagnostics, host-pointer copies) reports LBM_ERR_NONFINITE.
+ *   - Memory: the library owns the handle and a small internal block
+ *     (error flag, reduction partials, host staging).  The population and
+ *     scratch buffers are either bound by the caller (lbm_mix_bind_buffers;
+ *     the caller frees them after lbm_mix_destroy) or allocated by the
+ *     library (lbm_mix_alloc_buffers; freed by lbm_mix_destroy).
+ *   - Threading: a handle may be used by one host thread at a time.
+ */
+#ifndef LBM_MIX_H
+#define LBM_MIX_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,          /* invalid argument (message says which) */
+  LBM_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  LBM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  LBM_ERR_NONFINITE = 4,    /* a node reached rho <= 0, T <= 0 or NaN */
+  LBM_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  LBM_ERR_STATE = 6         /* call out of order (e.g. step before init) */
+} lbm_status;
+
+enum { LBM_BC_PERIODIC = 0 };
+enum { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_FP16_STORE = 2, LBM_PREC_BF16_STORE = 3 };
+enum { LBM_COUPLE_STRONG = 0, LBM_COUPLE_WEAK = 1 };
+enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
+
+/* Problem statement as the paper poses it (Secs. 2.1, 2.3, 3.1, 3.3, 3.5). */
+typedef struct {
+  int M;                      /* number of species, 1 <= M <= 8 (builds: 1,2,3,4,8) */
+  const double* molar_mass;   /* [M] m_a > 0; R_a = R_U / m_a (Eq. Ra) */
+  const double* cv_molar;     /* [M] C-bar_{a,v} / R_U > 0 (Sec. 3.1, constant) */
+  const double* D;            /* [M*M] row-major, symmetric binary diffusivities
+                                 D_ab > 0 (Eq. smDiffusionCoefficients2).  A
+                                 diagonal entry <= 0 selects the default
+                                 self-diffusivity: the geometric mean of the
+                                 row's off-diagonal entries (M = 1 needs D_11 > 0). */
+  const double* mu;           /* [M] species dynamic viscosities mu_a > 0 for the
+                                 Wilke rule (Eqs. viscosityMixture, wilkePhi);
+                                 may be NULL when omega_fixed > 0 */
+  const double* lambda;       /* [M] species conductivities lambda_a > 0 for the
+                                 Mathur rule (Eq. conductivityMixture); may be
+                                 NULL when omega1_fixed > 0 */
+  double omega_fixed;         /* > 0: constant omega instead of Eq. (omega) */
+  double omega1_fixed;        /* > 0: constant omega_1 instead of Eq. (omega1) */
+  double R_U;                 /* universal gas constant in lattice units (> 0) */
+  int nx, ny, nz;             /* grid, each >= 1 */
+  int bc[6];                  /* -x,+x,-y,+y,-z,+z; only LBM_BC_PERIODIC */
+  int slaved_species;         /* strong coupling: slaved index, -1 -> M-1 (Sec. 3.5.2) */
+  int precision;              /* LBM_PREC_* */
+  int coupling;               /* LBM_COUPLE_* */
+  int closure;                /* LBM_CLOSURE_* (only EXACT in this build) */
+  double fp64_cond_bound;     /* FP32 paths: solve the M x M system of Eq. (transform12)
+                                 in FP64 where its 1-norm condition bound exceeds this
+                                 (<= 0 -> 1e3) */
+} lbm_mix_params;
+
+typedef struct lbm_mix* lbm_mix_t;
+
+/* Validates `p`, derives the constant tables (Wilke phi_ab, 1/(D_ab m_a m_b),
+ * C_{a,v}, C_{a,p}) and creates a handle on the current CUDA device.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream) on which
+ * every later call is ordered.  Allocates only the small internal block. */
+LBM_API lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t* out);
+
+/* Bytes the caller must provide for the populations (S*27*N elements of the
+ * storage type) and the scratch side fields (8*N reals: Phi_alpha, 1/omega-1/2,
+ * C_p and G_alpha of Eq. Xalpha). */
+LBM_API lbm_status lbm_mix_required_bytes(lbm_mix_t h, size_t* pops_bytes, size_t* scratch_bytes);
+
+/* Binds caller-owned device buffers (at least the required sizes, 256-byte
+ * aligned).  The library never frees bound buffers. */
+LBM_API lbm_status lbm_mix_bind_buffers(lbm_mix_t h, void* pops, size_t pops_bytes,
+                                void* scratch, size_t scratch_bytes);
+
+/* Allocates the population and scratch buffers with cudaMalloc (freed by
+ * lbm_mix_destroy).  For callers without their own allocator. */
+LBM_API lbm_status lbm_mix_alloc_buffers(lbm_mix_t h);
+
+/* Equilibrium initial state (Eqs. 27eq, fixed, feq, gieq) from mole fractions
+ * X [M][N] (each node summing to 1), velocity u [3][N], temperature T [N] > 0
+ * and pressure P [N] > 0.  Resets the step counter to 0. */
+LBM_API lbm_status lbm_mix_init_fields(lbm_mix_t h, const double* X, const double* u,
+                               const double* T, const double* P, int host_ptrs);
+
+/* Advances nsteps >= 0 time steps (stream + collide of every lattice, Eqs.
+ * SMlbm, fwithcorrection, g) in place on the handle's stream (AA pattern:
+ * one read and one write of every population per step).  Asynchronous. */
+LBM_API lbm_status lbm_mix_step(lbm_mix_t h, int nsteps);
+
+/* Number of outputs of lbm_mix_get_moments for M species: 6 + 5*M. */
+LBM_API int lbm_mix_num_outputs(int M);
+
+/* Observables of the current state, [6+5M][N] float64:
+ * rho, u_x, u_y, u_z, T, P (Sec. 2.1, Eq. temperature2), X_1..X_M, Y_1..Y_M,
+ * then V_a (x,y,z) for a = 1..M, the diffusion velocities of Eq. (transform12)
+ * (species velocity u + V_a, Sec. 2.5.3). */
+LBM_API lbm_status lbm_mix_get_moments(lbm_mix_t h, double* out, int host_ptrs);
+
+/* Post-streaming populations of the current time level in natural layout
+ * [S][27][N] float64 (decoded from the storage precision).  With
+ * lbm_mix_set_populations this is the checkpoint / restart interface; set
+ * keeps the step counter (the in-place layout depends on its parity). */
+LBM_API lbm_status lbm_mix_get_populations(lbm_mix_t h, double* out, int host_ptrs);
+LBM_API lbm_status lbm_mix_set_populations(lbm_mix_t h, const double* in, int host_ptrs);
+
+/* Grid sums in float64, deterministic order, written to host sums[M+5]:
+ * sum rho_a of each stored species lattice (a = 1..M), sum rho, sum j (3)
+ * of the momentum lattice and sum rho*E of the energy lattice.
+ * Synchronises the stream and reports latched device errors. */
+LBM_API lbm_status lbm_mix_diagnostics(lbm_mix_t h, double* sums);
+
+/* Waits for the handle's stream; reports latched device errors. */
+LBM_API lbm_status lbm_mix_synchronize(lbm_mix_t h);
+
+/* Time steps taken since the last init_fields. */
+LBM_API long long lbm_mix_step_count(lbm_mix_t h);
+
+/* Kernel launches issued by this handle since creation (instrumentation). */
+LBM_API long long lbm_mix_launch_count(lbm_mix_t h);
+
+/* Instrumentation.  With timing enabled, every step records CUDA events on
+ * the handle's stream around each of its kernels (index 0: side fields,
+ * 1: G_alpha, 2: collide + stream).  lbm_mix_kernel_times synchronises, adds
+ * the elapsed times (ms) of all steps recorded since the previous query into
+ * ms[0..nk-1], writes the number of launches per kernel into counts, and
+ * forgets them.  Returns the number of kernels per step (3). */
+LBM_API lbm_status lbm_mix_enable_kernel_timing(lbm_mix_t h, int enable);
+LBM_API int lbm_mix_kernel_times(lbm_mix_t h, double* ms, long long* counts, int nk);
+
+/* Releases the handle, its internal block and library-allocated buffers. */
+LBM_API lbm_status lbm_mix_destroy(lbm_mix_t h);
+
+/* Message of the last error on `h` (or of the last failed create if h is NULL). */
+LBM_API const char* lbm_mix_last_error(lbm_mix_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_MIX_H */

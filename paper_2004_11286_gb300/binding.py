@@ -1,0 +1,266 @@
+"""Thin ctypes binding of ``include/lbm_mix.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (population and scratch buffers), pinned host
+buffers and the CUDA stream.  If the library is missing the constructor
+raises; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from pathlib import Path
+from typing import Optional
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "liblbm_mix.so"
+
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+COUPLING = {"strong": 0, "weak": 1}
+CLOSURE = {"exact": 0, "mlp": 1}
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_UNSUPPORTED", 3: "LBM_ERR_CUDA",
+          4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+_DP = ct.POINTER(ct.c_double)
+
+
+class lbm_mix_params(ct.Structure):
+    _fields_ = [
+        ("M", ct.c_int),
+        ("molar_mass", _DP), ("cv_molar", _DP), ("D", _DP), ("mu", _DP), ("lambda_", _DP),
+        ("omega_fixed", ct.c_double), ("omega1_fixed", ct.c_double), ("R_U", ct.c_double),
+        ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("bc", ct.c_int * 6),
+        ("slaved_species", ct.c_int), ("precision", ct.c_int), ("coupling", ct.c_int),
+        ("closure", ct.c_int),
+        ("fp64_cond_bound", ct.c_double),
+    ]
+
+
+# Every function the header declares: name -> (restype, argtypes).
+SIGNATURES = {
+    "lbm_mix_create": (ct.c_int, [ct.POINTER(lbm_mix_params), ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "lbm_mix_required_bytes": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)]),
+    "lbm_mix_bind_buffers": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_size_t]),
+    "lbm_mix_alloc_buffers": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_init_fields": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_step": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_mix_num_outputs": (ct.c_int, [ct.c_int]),
+    "lbm_mix_get_moments": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_get_populations": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_set_populations": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_diagnostics": (ct.c_int, [ct.c_void_p, _DP]),
+    "lbm_mix_synchronize": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_step_count": (ct.c_longlong, [ct.c_void_p]),
+    "lbm_mix_launch_count": (ct.c_longlong, [ct.c_void_p]),
+    "lbm_mix_enable_kernel_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_mix_kernel_times": (ct.c_int, [ct.c_void_p, _DP, ct.POINTER(ct.c_longlong), ct.c_int]),
+    "lbm_mix_destroy": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_last_error": (ct.c_char_p, [ct.c_void_p]),
+}
+
+_lib: Optional[ct.CDLL] = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: Optional[os.PathLike] = None) -> ct.CDLL:
+    """Load ``liblbm_mix.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path is not None else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"{p} is missing: build it with paper_2004_11286_gb300.build.build()")
+    lib = ct.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_DP)
+
+
+class LbmMix:
+    """One simulation handle: a periodic nz x ny x nx grid of M species + f + g.
+
+    Fields cross the boundary as float64 arrays: NumPy arrays are host
+    pointers, torch CUDA tensors are device pointers.
+    """
+
+    def __init__(self, molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1),
+                 precision: str = "fp32", coupling: str = "strong", slaved: int = -1,
+                 omega_fixed: float = 0.0, omega1_fixed: float = 0.0, R_U: float = 1.0,
+                 fp64_cond_bound: float = 0.0, closure: str = "exact", device=None, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.M = int(len(molar_mass))
+        self.shape = tuple(int(s) for s in shape)
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self._keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
+                      for v in (molar_mass, cv_molar, D)]
+        mu_a = None if mu is None else np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+        lam_a = None if lam is None else np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        self._keep += [mu_a, lam_a]
+        p = lbm_mix_params()
+        p.M = self.M
+        p.molar_mass, p.cv_molar, p.D = (_dp(a) for a in self._keep[:3])
+        p.mu = _dp(mu_a)
+        p.lambda_ = _dp(lam_a)
+        p.omega_fixed, p.omega1_fixed, p.R_U = float(omega_fixed), float(omega1_fixed), float(R_U)
+        p.nx, p.ny, p.nz = nx, ny, nz
+        for s in range(6):
+            p.bc[s] = 0
+        p.slaved_species = int(slaved)
+        p.precision = PREC[precision]
+        p.coupling = COUPLING[coupling]
+        p.closure = CLOSURE[closure]
+        p.fp64_cond_bound = float(fp64_cond_bound)
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ct.c_void_p()
+            st = self.lib.lbm_mix_create(ct.byref(p), ct.c_void_p(self.stream.cuda_stream), ct.byref(h))
+            if st != 0:
+                raise LbmError(st, self.lib.lbm_mix_last_error(None).decode())
+            self.h = h
+            pb, sb = ct.c_size_t(), ct.c_size_t()
+            self._check(self.lib.lbm_mix_required_bytes(self.h, ct.byref(pb), ct.byref(sb)))
+            self.pops_buf = torch.empty(pb.value, dtype=torch.uint8, device=self.device)
+            self.scratch_buf = torch.empty(sb.value, dtype=torch.uint8, device=self.device)
+            self._check(self.lib.lbm_mix_bind_buffers(self.h, ct.c_void_p(self.pops_buf.data_ptr()), pb.value,
+                                                      ct.c_void_p(self.scratch_buf.data_ptr()), sb.value))
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise LbmError(st, self.lib.lbm_mix_last_error(self.h).decode())
+
+    def _ptr(self, a, n_expected: int):
+        """(pointer, host_flag, keepalive) for a float64 array of n elements."""
+        torch = self._torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n_expected:
+                raise ValueError("expected a contiguous float64 tensor of %d elements" % n_expected)
+            if a.is_cuda:
+                return ct.c_void_p(a.data_ptr()), 0, a
+            return ct.c_void_p(a.data_ptr()), 1, a
+        arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        if arr.size != n_expected:
+            raise ValueError("expected %d elements, got %d" % (n_expected, arr.size))
+        return ct.c_void_p(arr.ctypes.data), 1, arr
+
+    # -- API -----------------------------------------------------------------
+    def init_fields(self, X, u, T, P):
+        N, M = self.N, self.M
+        px, hx, kx = self._ptr(X, M * N)
+        pu, hu, ku = self._ptr(u, 3 * N)
+        pt, ht, kt = self._ptr(T, N)
+        pp, hp, kp = self._ptr(P, N)
+        if len({hx, hu, ht, hp}) != 1:
+            raise ValueError("X, u, T, P must all be host arrays or all device tensors")
+        self._check(self.lib.lbm_mix_init_fields(self.h, px, pu, pt, pp, hx))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbm_mix_step(self.h, int(n)))
+
+    @property
+    def n_outputs(self) -> int:
+        return int(self.lib.lbm_mix_num_outputs(self.M))
+
+    def moments(self, out=None):
+        """Observables [6+5M][N] (float64): NumPy on the host unless ``out``
+        is a device tensor."""
+        n = self.n_outputs * self.N
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        p, host, keep = self._ptr(out, n)
+        self._check(self.lib.lbm_mix_get_moments(self.h, p, host))
+        return out
+
+    def moments_dict(self):
+        nz, ny, nx = self.shape
+        M = self.M
+        o = self.moments().reshape(self.n_outputs, nz, ny, nx)
+        return dict(rho=o[0], u=o[1:4], T=o[4], P=o[5], X=o[6:6 + M], Y=o[6 + M:6 + 2 * M],
+                    V=o[6 + 2 * M:].reshape(M, 3, nz, ny, nx))
+
+    def populations(self, out=None):
+        n = (self.M + 2) * 27 * self.N
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        p, host, keep = self._ptr(out, n)
+        self._check(self.lib.lbm_mix_get_populations(self.h, p, host))
+        if isinstance(out, np.ndarray):
+            return out.reshape((self.M + 2, 27) + self.shape)
+        return out
+
+    def set_populations(self, pops):
+        n = (self.M + 2) * 27 * self.N
+        p, host, keep = self._ptr(pops, n)
+        self._check(self.lib.lbm_mix_set_populations(self.h, p, host))
+
+    def diagnostics(self):
+        out = np.empty(self.M + 5, dtype=np.float64)
+        self._check(self.lib.lbm_mix_diagnostics(self.h, out.ctypes.data_as(_DP)))
+        return out
+
+    def synchronize(self):
+        self._check(self.lib.lbm_mix_synchronize(self.h))
+
+    KERNEL_NAMES = ("side_fields", "grad_G", "collide_stream")
+
+    def enable_kernel_timing(self, on: bool = True):
+        self._check(self.lib.lbm_mix_enable_kernel_timing(self.h, int(bool(on))))
+
+    def kernel_times(self):
+        """{kernel: (total_ms, launches)} for the steps recorded since the last query."""
+        ms = np.zeros(3)
+        cnt = (ct.c_longlong * 3)()
+        n = self.lib.lbm_mix_kernel_times(self.h, ms.ctypes.data_as(_DP), cnt, 3)
+        if n < 0:
+            raise LbmError(3, "kernel_times failed")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_NAMES)}
+
+    @property
+    def step_count(self) -> int:
+        return int(self.lib.lbm_mix_step_count(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.lbm_mix_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_mix_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_workload(wl, precision: str = "fp32", **kw) -> LbmMix:
+    """Handle for a ``workloads.Workload`` (periodic grid, its species constants)."""
+    params = wl.params()
+    return LbmMix(params["molar_mass"], params["cv_molar"], params["D"], mu=params["mu"],
+                  lam=params["lam"], shape=wl.shape, precision=precision, R_U=params["R_U"], **kw)

@@ -1,0 +1,306 @@
+// lbm_device.cuh -- per-node device arithmetic of the multicomponent D3Q27
+// lattice Boltzmann step (Sawant, Dorschner & Karlin, arXiv 2004.11286).
+//
+// Everything here is templated on the species count M (compile-time, so the
+// per-node state lives in registers) and on the arithmetic type Real
+// (double for the FP64 path, float otherwise).  The storage type of the
+// populations is handled by the codec in lbm_codec.cuh.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 27;
+constexpr int MAXM = 8;
+constexpr int NSIDE = 8;   // side-field planes: Phi_x,Phi_y,Phi_z, c_omega, C_p, G_x,G_y,G_z
+
+// Velocity i = (cx+1) + 3(cy+1) + 9(cz+1), Eq. (d3q27vel).
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz_of(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr int c2_of(int i) {
+  return cx_of(i) * cx_of(i) + cy_of(i) * cy_of(i) + cz_of(i) * cz_of(i);
+}
+__host__ __device__ constexpr int opp_of(int i) { return 26 - i; }
+__host__ __device__ constexpr int c_of(int i, int a) {
+  return a == 0 ? cx_of(i) : (a == 1 ? cy_of(i) : cz_of(i));
+}
+
+// Isotropic D3Q27 gradient weights (second-order isotropic operator of Sec. 4.1):
+// d_a phi(x) = 3 sum_i w_i c_ia phi(x + c_i).
+template <class Real>
+__host__ __device__ constexpr Real iso_w(int i) {
+  return c2_of(i) == 0 ? Real(8) / Real(27)
+       : c2_of(i) == 1 ? Real(2) / Real(27)
+       : c2_of(i) == 2 ? Real(1) / Real(54) : Real(1) / Real(216);
+}
+
+// Constants derived on the host from the problem statement.
+template <class Real>
+struct DevParams {
+  long long N;
+  int nx, ny, nz;
+  int M;
+  int slaved;            // strong coupling: slaved species index
+  int weak;              // 1 = weak coupling (Sec. 3.5.1)
+  int omega_is_fixed, omega1_is_fixed;
+  Real omega_fixed, omega1_fixed;
+  Real R_U;
+  Real rho_eps;          // V_a = 0 where rho_a <= rho_eps * rho
+  Real cond_bound;       // FP64 re-solve threshold for the SM system (FP32 paths)
+  Real mass[MAXM];
+  Real inv_mass[MAXM];
+  Real R_a[MAXM];
+  Real Cv_a[MAXM];
+  Real Cp_a[MAXM];
+  Real mu[MAXM];
+  Real lam[MAXM];
+  Real inv_lam[MAXM];
+  Real phi[MAXM][MAXM];  // Wilke factors, Eq. (wilkePhi)
+  Real Cab[MAXM][MAXM];  // 1 / (D_ab m_a m_b): 1/tau_ab = R_U T m Cab (Eq. tauab)
+  double Cab64[MAXM][MAXM];
+};
+
+// ---------------------------------------------------------------------------
+// Product form, Sec. 2.4: triplets Psi_0, Psi_{+1}, Psi_{-1}.
+// ---------------------------------------------------------------------------
+template <class Real>
+struct Triplet { Real m, z, p; };   // values for c = -1, 0, +1
+
+template <class Real>
+__device__ __forceinline__ Triplet<Real> psi_triplet(Real xi, Real zeta) {
+  Real s = xi * xi + zeta;
+  Triplet<Real> t;
+  t.z = Real(1) - s;
+  t.p = Real(0.5) * (s + xi);
+  t.m = Real(0.5) * (s - xi);
+  return t;
+}
+
+template <class Real>
+__device__ __forceinline__ Real tri(const Triplet<Real>& t, int c) {
+  return c < 0 ? t.m : (c == 0 ? t.z : t.p);
+}
+
+// ---------------------------------------------------------------------------
+// Grid addressing.
+// ---------------------------------------------------------------------------
+struct Nbr {
+  long long xs[3], ys[3], zs[3];  // wrapped coordinates for offsets -1, 0, +1 (y,z pre-scaled)
+  __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
+    return zs[dz + 1] + ys[dy + 1] + xs[dx + 1];
+  }
+};
+
+template <class Real>
+__device__ __forceinline__ Nbr make_nbr(const DevParams<Real>& p, long long n) {
+  Nbr b;
+  long long nx = p.nx, ny = p.ny, nz = p.nz;
+  long long x = n % nx;
+  long long t = n / nx;
+  long long y = t % ny;
+  long long z = t / ny;
+  b.xs[0] = x == 0 ? nx - 1 : x - 1;  b.xs[1] = x;  b.xs[2] = x == nx - 1 ? 0 : x + 1;
+  b.ys[0] = (y == 0 ? ny - 1 : y - 1) * nx;  b.ys[1] = y * nx;  b.ys[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+  b.zs[0] = (z == 0 ? nz - 1 : z - 1) * nx * ny;  b.zs[1] = z * nx * ny;
+  b.zs[2] = (z == nz - 1 ? 0 : z + 1) * nx * ny;
+  return b;
+}
+
+// AA pattern.  parity 0 (even time level): logical population i of node x
+// lives in slot i of x; the collision writes its result for direction i to
+// slot opp(i) of x.  parity 1: logical population i of x lives in slot
+// opp(i) of x - c_i; the collision writes direction i to slot i of x + c_i.
+// Each node reads and writes the same set of addresses in a step.
+__device__ __forceinline__ void aa_read_loc(int parity, const Nbr& nb, long long n, int i,
+                                            long long& node, int& slot) {
+  if (parity == 0) { node = n; slot = i; }
+  else { node = nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)); slot = opp_of(i); }
+}
+__device__ __forceinline__ void aa_write_loc(int parity, const Nbr& nb, long long n, int i,
+                                             long long& node, int& slot) {
+  if (parity == 0) { node = n; slot = opp_of(i); }
+  else { node = nb.idx(cx_of(i), cy_of(i), cz_of(i)); slot = i; }
+}
+
+// ---------------------------------------------------------------------------
+// Per-node thermodynamic state (Secs. 2.1, 3.1, 3.3, 3.5).
+// ---------------------------------------------------------------------------
+template <int M, class Real>
+struct Thermo {
+  Real rho_a[M];      // coupled species densities
+  Real Y[M];
+  Real rho_sp;        // density seen by the species (rho under strong coupling)
+  Real m, R, Cv, Cp, T, P, usq;
+  Real u[3];          // mixture velocity (momentum lattice)
+  Real u_sp[3];       // velocity seen by the species
+  Real omega;
+};
+
+// Coupling, composition, caloric closure and omega.  rho_a_raw are the
+// species zeroth moments (the slaved entry is ignored under strong coupling),
+// ja_sum the sum of species momenta (used under weak coupling only).
+template <int M, class Real>
+__device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Real (&rho_a_raw)[M],
+                                             const Real (&ja_sum)[3], Real rho, const Real (&j)[3],
+                                             Real rhoE, Thermo<M, Real>& th) {
+  Real inv_rho = Real(1) / rho;
+  th.u[0] = j[0] * inv_rho; th.u[1] = j[1] * inv_rho; th.u[2] = j[2] * inv_rho;
+  if (!p.weak) {
+    // Eqs. (rhoMATCH), (uMATCH): the slaved species takes the deficit.
+    Real others = Real(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) if (a != p.slaved) others += rho_a_raw[a];
+#pragma unroll
+    for (int a = 0; a < M; ++a) th.rho_a[a] = (a == p.slaved) ? rho - others : rho_a_raw[a];
+    th.rho_sp = rho;
+    th.u_sp[0] = th.u[0]; th.u_sp[1] = th.u[1]; th.u_sp[2] = th.u[2];
+  } else {
+    Real s = Real(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) { th.rho_a[a] = rho_a_raw[a]; s += rho_a_raw[a]; }
+    th.rho_sp = s;
+    Real is = Real(1) / s;
+    th.u_sp[0] = ja_sum[0] * is; th.u_sp[1] = ja_sum[1] * is; th.u_sp[2] = ja_sum[2] * is;
+  }
+  Real inv_sp = Real(1) / th.rho_sp;
+  Real inv_m = Real(0), Cv = Real(0), Cp = Real(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    th.Y[a] = th.rho_a[a] * inv_sp;                      // Eq. (mixtureDensity)
+    inv_m += th.Y[a] * p.inv_mass[a];                    // Eq. (meanMolecularWeight)
+    Cv += th.Y[a] * p.Cv_a[a];                           // Eq. (Cvmix)
+    Cp += th.Y[a] * p.Cp_a[a];
+  }
+  th.m = Real(1) / inv_m;
+  th.R = p.R_U * inv_m;                                  // Eq. (defineSpecificGasContant)
+  th.Cv = Cv; th.Cp = Cp;
+  th.usq = th.u[0] * th.u[0] + th.u[1] * th.u[1] + th.u[2] * th.u[2];
+  th.T = (rhoE * inv_rho - Real(0.5) * th.usq) / Cv;    // Eq. (temperature2), T0 = 0
+  th.P = rho * th.R * th.T;                              // Eq. (eosIdealGas)
+  if (p.omega_is_fixed) {
+    th.omega = p.omega_fixed;
+  } else {
+    // Wilke, Eqs. (viscosityMixture), (wilkePhi); X_a = m Y_a / m_a.
+    Real X[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) X[a] = th.m * th.Y[a] * p.inv_mass[a];
+    Real mu = Real(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      Real den = Real(0);
+#pragma unroll
+      for (int b = 0; b < M; ++b) den += p.phi[a][b] * X[b];
+      mu += p.mu[a] * X[a] / den;
+    }
+    th.omega = Real(2) * th.P / (th.P + Real(2) * mu);   // Eq. (omega)
+  }
+}
+
+template <int M, class Real>
+__device__ __forceinline__ Real omega1_of(const DevParams<Real>& p, const Thermo<M, Real>& th) {
+  if (p.omega1_is_fixed) return p.omega1_fixed;
+  // Mathur, Eq. (conductivityMixture); Eq. (omega1).
+  Real s1 = Real(0), s2 = Real(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    Real X = th.m * th.Y[a] * p.inv_mass[a];
+    s1 += X * p.lam[a];
+    s2 += X * p.inv_lam[a];
+  }
+  Real lam = Real(0.5) * (s1 + Real(1) / s2);
+  Real pc = th.P * th.Cp;
+  return Real(2) * pc / (pc + Real(2) * lam);
+}
+
+// ---------------------------------------------------------------------------
+// Stefan-Maxwell diffusion fluxes J_a = rho_a V_a from Eq. (transform12),
+// written for J (well posed when rho_a -> 0):
+//   J_a + 1/2 sum_{b != a} (1/tau_ab) (Y_b J_a - Y_a J_b) = j_a - rho_a u.
+// The matrix is I plus a singular column-diagonally-dominant M-matrix
+// (columns sum to one), so elimination without pivoting is stable; its
+// 1-norm condition number is bounded by 1 + max_b sum_{a != b} Y_a/tau_ab.
+// ---------------------------------------------------------------------------
+template <int M, class T>
+__device__ __forceinline__ void sm_eliminate(T (&A)[M][M], T (&r)[M][3], T (&J)[M][3]) {
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    T inv = T(1) / A[k][k];
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      T l = A[i][k] * inv;
+#pragma unroll
+      for (int jj = k + 1; jj < M; ++jj) A[i][jj] -= l * A[k][jj];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[i][c] -= l * r[k][c];
+    }
+  }
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T s = r[k][c];
+#pragma unroll
+      for (int jj = k + 1; jj < M; ++jj) s -= A[k][jj] * J[jj][c];
+      J[k][c] = s / A[k][k];
+    }
+  }
+}
+
+template <int M, class Real>
+__device__ __forceinline__ void sm_solve(const DevParams<Real>& p, const Thermo<M, Real>& th,
+                                         const Real (&itab)[M][M], const Real (&ja)[M][3],
+                                         Real (&J)[M][3]) {
+  Real A[M][M], r[M][3];
+  Real cond = Real(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    Real diag = Real(1);
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      if (b != a) {
+        diag += Real(0.5) * itab[a][b] * th.Y[b];
+        A[a][b] = Real(-0.5) * itab[a][b] * th.Y[a];
+      }
+    }
+    A[a][a] = diag;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[a][c] = ja[a][c] - th.rho_a[a] * th.u_sp[c];
+    cond = fmax(cond, Real(2) * (diag - Real(1)));
+  }
+  if constexpr (sizeof(Real) == 4) {
+    if (cond + Real(1) > p.cond_bound) {
+    // Ill-conditioned system in the FP32 paths: re-solve in FP64.
+    double A64[M][M], r64[M][3], J64[M][3];
+    double T = (double)th.T, m = (double)th.m;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      double diag = 1.0;
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        if (b != a) {
+          double it = (double)p.R_U * T * m * p.Cab64[a][b];
+          diag += 0.5 * it * (double)th.Y[b];
+          A64[a][b] = -0.5 * it * (double)th.Y[a];
+        }
+      }
+      A64[a][a] = diag;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r64[a][c] = (double)ja[a][c] - (double)th.rho_a[a] * (double)th.u_sp[c];
+    }
+    sm_eliminate<M, double>(A64, r64, J64);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) J[a][c] = (Real)J64[a][c];
+    return;
+    }
+  }
+  sm_eliminate<M, Real>(A, r, J);
+}
+
+}  // namespace lbm

@@ -1,0 +1,110 @@
+"""The C-ABI library loads on a machine without a GPU and exports every symbol
+``include/lbm_mix.h`` declares; the ctypes mirror of ``lbm_mix_params``
+matches the C layout; argument validation fails cleanly before any CUDA call."""
+
+import ctypes as ct
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm_mix.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"LBM_API\s+[\w\s\*]+?\b(lbm_mix_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["lbm_mix_create", "lbm_mix_init_fields", "lbm_mix_step", "lbm_mix_get_moments",
+                     "lbm_mix_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built_library):
+    lib = ct.CDLL(str(built_library))
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", str(built_library)], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(lbm_mix_\w+)\b", out))
+    assert exported == set(_declared())
+
+
+def test_binding_mirrors_header(built_library):
+    from paper_2004_11286_gb300 import binding
+    assert set(binding.SIGNATURES) == set(_declared())
+    lib = binding.load_library()
+    assert lib.lbm_mix_num_outputs(3) == 6 + 5 * 3
+
+
+def test_params_struct_layout(tmp_path):
+    from paper_2004_11286_gb300.binding import lbm_mix_params
+    c = tmp_path / "layout.c"
+    c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm_mix.h"\n'
+                 "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(lbm_mix_params),"
+                 " offsetof(lbm_mix_params, omega_fixed), offsetof(lbm_mix_params, nx),"
+                 " offsetof(lbm_mix_params, slaved_species), offsetof(lbm_mix_params, fp64_cond_bound));"
+                 "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    P = lbm_mix_params
+    assert vals == [ct.sizeof(P), P.omega_fixed.offset, P.nx.offset, P.slaved_species.offset,
+                    P.fp64_cond_bound.offset]
+
+
+def _params(M=2, **over):
+    from paper_2004_11286_gb300.binding import lbm_mix_params, _DP
+    import numpy as np
+    keep = [np.array([4.0, 40.0][:M]), np.array([1.5, 1.5][:M]), np.array([[0, .05], [.05, 0]])[:M, :M].ravel().copy(),
+            np.array([0.003, 0.003][:M]), np.array([0.01, 0.01][:M])]
+    p = lbm_mix_params()
+    p.M = M
+    p.molar_mass, p.cv_molar, p.D, p.mu, p.lambda_ = (a.ctypes.data_as(_DP) for a in keep)
+    p.R_U, p.nx, p.ny, p.nz = 1.0, 8, 8, 8
+    p.slaved_species, p.precision, p.coupling, p.closure = -1, 1, 0, 0
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p, keep
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("M", 0, 1), ("M", 9, 1), ("nx", 0, 1), ("R_U", 0.0, 1), ("precision", 7, 1),
+    ("coupling", 5, 1), ("closure", 3, 2), ("slaved_species", 4, 1),
+])
+def test_create_rejects_bad_arguments_without_touching_cuda(built_library, field, value, status):
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    p, keep = _params(**{field: value})
+    h = ct.c_void_p()
+    st = lib.lbm_mix_create(ct.byref(p), None, ct.byref(h))
+    assert st == status
+    assert h.value is None
+    assert lib.lbm_mix_last_error(None).decode()
+
+
+def test_create_rejects_nonperiodic_and_asymmetric(built_library):
+    from paper_2004_11286_gb300 import binding
+    import numpy as np
+    lib = binding.load_library()
+    p, keep = _params()
+    p.bc[1] = 1
+    h = ct.c_void_p()
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == 2
+    p, keep = _params()
+    bad = np.array([0, .05, .06, 0.0])
+    p.D = bad.ctypes.data_as(binding._DP)
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == 1
+    assert "symmetric" in lib.lbm_mix_last_error(None).decode()
+
+
+def test_null_handle_calls_fail_cleanly(built_library):
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    assert lib.lbm_mix_step(None, 1) == 1
+    assert lib.lbm_mix_destroy(None) == 1
+    assert lib.lbm_mix_step_count(None) == -1

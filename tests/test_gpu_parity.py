@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 mode 1e-12 relative, FP32 mode 1e-5 relative on density,
+velocity (floored at 1e-3 c_s), temperature, pressure and mole fractions
+(absolute), as the method's precision contract states; populations compared
+relative to their largest magnitude.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_11286_gb300 import workloads as W
+
+from gpu_helpers import TOL, field_errors, gpu_handle, oracle_params, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2004_11286_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def _perturbed_state(wl, prm, seed, scale=0.01):
+    pops = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm)
+    return pops * W.perturbation(pops.shape, scale, seed)
+
+
+def _oracle_moments(pops, prm):
+    mac = O.macroscopic(pops, prm)
+    return dict(rho=mac["rho"], u=mac["u"], T=mac["T"], P=mac["P"], X=mac["X"], Y=mac["Y"], V=mac["V"])
+
+
+def _cs(wl):
+    mbar = float(np.dot(wl.X.reshape(wl.M, -1).mean(axis=1), wl.molar_mass))
+    return np.sqrt(1.4 * wl.T.mean() / mbar)
+
+
+# ---------------------------------------------------------------------------
+# Ragged grids, random off-equilibrium states, both AA parities.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("M,coupling", [(1, "strong"), (2, "strong"), (3, "strong"), (3, "weak"),
+                                        (4, "strong"), (8, "strong"), (8, "weak")])
+def test_ragged_random_state_steps(M, coupling, precision):
+    wl = W.random_mixture(M=M, shape=(5, 7, 13), seed=100 + M, velocity=0.03)
+    prm = oracle_params(wl, coupling=coupling)
+    pops = _perturbed_state(wl, prm, seed=M)
+    h = gpu_handle(wl, precision, coupling=coupling)
+    h.set_populations(pops)
+    stored = pops if precision == "fp64" else pops.astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(h.populations(), stored)
+    ref = pops
+    for k in range(3):                     # steps at parity 0, 1, 0
+        ref = O.step(ref, prm)
+        h.step(1)
+        got = h.populations()
+        e = rel(got, ref)
+        assert e < TOL[precision], (k, e)
+        gm, om = h.moments_dict(), _oracle_moments(ref, prm)
+        errs = field_errors(gm, om, _cs(wl))
+        assert max(errs.values()) < TOL[precision], (k, errs)
+        # diffusion velocities: relative to their size, floored like u
+        assert rel(gm["V"], om["V"], floor=1e-3 * _cs(wl)) < 10 * TOL[precision], k
+    h.close()
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 8])
+def test_init_fields_matches_oracle(M):
+    wl = W.random_mixture(M=M, shape=(3, 6, 11), seed=7 + M, velocity=0.05)
+    prm = oracle_params(wl)
+    h = gpu_handle(wl, "fp64")
+    h.init_fields(wl.X, wl.u, wl.T, wl.P)
+    ref = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm)
+    assert rel(h.populations(), ref) < 1e-14
+    gm = h.moments_dict()
+    np.testing.assert_allclose(gm["T"], wl.T, rtol=1e-13)
+    np.testing.assert_allclose(gm["P"], wl.P, rtol=1e-13)
+    np.testing.assert_allclose(gm["X"], wl.X, atol=1e-14)
+    h.close()
+
+
+def test_checkpoint_roundtrip_is_bit_exact():
+    wl = W.random_mixture(M=3, shape=(4, 5, 6), seed=3)
+    prm = oracle_params(wl)
+    pops = _perturbed_state(wl, prm, seed=9)
+    h = gpu_handle(wl, "fp64")
+    h.set_populations(pops)
+    h.step(1)                                   # odd parity: AA layout differs from natural
+    a = h.populations()
+    h.set_populations(a)
+    np.testing.assert_array_equal(h.populations(), a)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Full horizons of the ternary tube (64 x 4 x 4, 1000 steps) and of a reduced
+# acoustic pulse.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def tube_reference():
+    wl = W.ternary_tube()
+    prm = oracle_params(wl)
+    pops = O.run(O.init_populations(wl.X, wl.u, wl.T, wl.P, prm), prm, wl.steps)
+    return wl, prm, pops
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ternary_tube_full_horizon(tube_reference, precision):
+    wl, prm, ref = tube_reference
+    h = gpu_handle(wl, precision)
+    h.init_fields(wl.X, wl.u, wl.T, wl.P)
+    h.step(wl.steps)
+    errs = field_errors(h.moments_dict(), _oracle_moments(ref, prm), _cs(wl))
+    assert max(errs.values()) < TOL[precision], errs
+    if precision == "fp64":
+        assert rel(h.populations(), ref) < TOL["fp64"]
+    h.close()
+
+
+def test_acoustic_pulse_reduced_full_horizon_fp32():
+    wl = W.acoustic_pulse(shape=(12, 14, 16), sigma=2.0, steps=2000)
+    prm = oracle_params(wl)
+    ref = O.run(O.init_populations(wl.X, wl.u, wl.T, wl.P, prm), prm, wl.steps)
+    h = gpu_handle(wl, "fp32")
+    h.init_fields(wl.X, wl.u, wl.T, wl.P)
+    h.step(wl.steps)
+    errs = field_errors(h.moments_dict(), _oracle_moments(ref, prm), _cs(wl))
+    assert max(errs.values()) < TOL["fp32"], errs
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Full size, the configuration the benchmark times (128^3 binary acoustic
+# pulse, FP32): one step checked on sampled nodes against the oracle's
+# per-node evaluation on a periodic neighbourhood.
+# ---------------------------------------------------------------------------
+def test_full_size_sampled_step_fp32():
+    wl = W.acoustic_pulse()
+    prm = oracle_params(wl)
+    h = gpu_handle(wl, "fp32")
+    h.init_fields(wl.X, wl.u, wl.T, wl.P)
+    h.step(20)
+    before = h.populations().astype(np.float64)
+    h.step(1)
+    after = h.populations()
+    nz, ny, nx = wl.shape
+    rng = np.random.Generator(np.random.PCG64(77))
+    samples = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz // 2, ny // 2, nx // 2), (nz // 2 + 3, ny // 2 - 5, nx // 2 + 6)]
+    samples += [tuple(int(v) for v in rng.integers(0, s)) for s in [(nz, ny, nx)] * 24]
+    C = O.C
+    scale = np.abs(before).max()
+    for (z, y, x) in samples:
+        post = O.collide_patch_center(before, z, y, x, prm)          # (S, 27)
+        for i in range(27):
+            dz, dy, dx = (z + C[i, 2]) % nz, (y + C[i, 1]) % ny, (x + C[i, 0]) % nx
+            got = after[:, i, dz, dy, dx]
+            assert np.abs(got - post[:, i]).max() / scale < 2e-6, ((z, y, x), i)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Conservation diagnostics (FP64 sums), errors latched on the device.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diagnostics_match_oracle_and_conserve(precision):
+    wl = W.random_mixture(M=3, shape=(9, 10, 11), seed=5, velocity=0.02)
+    prm = oracle_params(wl)
+    pops = _perturbed_state(wl, prm, seed=2)
+    h = gpu_handle(wl, precision)
+    h.set_populations(pops)
+    s0 = h.diagnostics()
+    np.testing.assert_allclose(s0, O.conserved_sums(pops, prm), rtol=1e-12 if precision == "fp64" else 1e-6,
+                               atol=1e-9)
+    h.step(7)
+    s1 = h.diagnostics()
+    keep = [a for a in range(3) if a != prm.slaved] + [3, 7]   # unslaved species, rho, rhoE
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    np.testing.assert_allclose(s1[keep], s0[keep], rtol=tol)
+    np.testing.assert_allclose(s1[4:7], s0[4:7], atol=tol * s0[3])    # momentum
+    h.close()
+
+
+def test_nonfinite_state_is_reported():
+    from paper_2004_11286_gb300.binding import LbmError
+    wl = W.random_mixture(M=2, shape=(4, 4, 4), seed=1)
+    prm = oracle_params(wl)
+    pops = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm)
+    pops[2, :, 1, 2, 3] = -pops[2, :, 1, 2, 3]          # negative mixture density at one node
+    h = gpu_handle(wl, "fp64")
+    h.set_populations(pops)
+    h.step(1)
+    with pytest.raises(LbmError) as e:
+        h.synchronize()
+    assert e.value.status == 4
+    h.close()
+
+
+def test_step_before_state_is_rejected():
+    from paper_2004_11286_gb300.binding import LbmError
+    wl = W.random_mixture(M=2, shape=(4, 4, 4), seed=1)
+    h = gpu_handle(wl, "fp32")
+    with pytest.raises(LbmError) as e:
+        h.step(1)
+    assert e.value.status == 6
+    h.close()
