@@ -9,7 +9,6 @@
 
 #include "../../include/lbm_mix.h"
 #include "lbm_device.cuh"
-#include "lbm_codec.cuh"
 #include "lbm_dispatch.h"
 
 namespace {
@@ -17,14 +16,24 @@ namespace {
 thread_local std::string g_create_error;
 
 const lbm::KernelSet* select_kernels(int M, int prec) {
+#define LBM_PICK(MM)                                   \
+  case MM:                                             \
+    switch (prec) {                                    \
+      case LBM_PREC_FP64: return lbm::kernel_set_m##MM##_f64();        \
+      case LBM_PREC_FP32: return lbm::kernel_set_m##MM##_f32();        \
+      case LBM_PREC_FP16_STORE: return lbm::kernel_set_m##MM##_f16();  \
+      case LBM_PREC_BF16_STORE: return lbm::kernel_set_m##MM##_bf16(); \
+      default: return nullptr;                         \
+    }
   switch (M) {
-    case 1: return lbm::kernel_set_m1(prec);
-    case 2: return lbm::kernel_set_m2(prec);
-    case 3: return lbm::kernel_set_m3(prec);
-    case 4: return lbm::kernel_set_m4(prec);
-    case 8: return lbm::kernel_set_m8(prec);
+    LBM_PICK(1)
+    LBM_PICK(2)
+    LBM_PICK(3)
+    LBM_PICK(4)
+    LBM_PICK(8)
     default: return nullptr;
   }
+#undef LBM_PICK
 }
 
 size_t store_elem_bytes(int prec) { return prec == LBM_PREC_FP64 ? 8 : (prec == LBM_PREC_FP32 ? 4 : 2); }
@@ -44,6 +53,81 @@ void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
       d.phi[a][b] = (Real)s.phi[a][b]; d.Cab[a][b] = (Real)s.Cab[a][b]; d.Cab64[a][b] = s.Cab64[a][b];
     }
   }
+  for (int L = 0; L < lbm::MAXM + 2; ++L) {
+    d.RL[L] = (Real)s.RL[L]; d.scale[L] = (Real)s.scale[L]; d.inv_scale[L] = (Real)s.inv_scale[L];
+  }
+  for (int a = 0; a < lbm::MAXM; ++a) d.Yr[a] = (Real)s.Yr[a];
+  d.Tr = (Real)s.Tr; d.Rr = (Real)s.Rr; d.thr = (Real)s.thr; d.Pr = (Real)s.Pr; d.Cvr = (Real)s.Cvr;
+  d.cE = (Real)s.cE; d.cPi = (Real)s.cPi; d.cS = (Real)s.cS; d.Rsp = (Real)s.Rsp;
+}
+
+// Reductions used to pick the reference state: per-block partial sums of
+// nv values per node, then a fixed-order final sum (deterministic).
+constexpr int RED_BLOCK = 256;
+constexpr int RED_MAXV = 16;
+
+__device__ __forceinline__ double red_warp(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void red_block_store(double (&v)[RED_MAXV], int nv, double* partials) {
+  __shared__ double red[RED_BLOCK / 32][RED_MAXV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int s = 0; s < nv; ++s) {
+    const double t = red_warp(v[s]);
+    if (lane == 0) red[wid][s] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int w = 0; w < RED_BLOCK / 32; ++w) t += red[w][threadIdx.x];
+    partials[(long long)blockIdx.x * nv + threadIdx.x] = t;
+  }
+}
+
+// sums of X_a (a < M), T and P over the nodes
+__global__ void __launch_bounds__(RED_BLOCK)
+field_partials_kernel(const double* __restrict__ X, const double* __restrict__ T, const double* __restrict__ P,
+                      int M, long long N, double* __restrict__ partials) {
+  double v[RED_MAXV];
+  for (int s = 0; s < RED_MAXV; ++s) v[s] = 0.0;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N) {
+    for (int a = 0; a < M; ++a) v[a] = X[a * N + n];
+    v[M] = T[n];
+    v[M + 1] = P[n];
+  }
+  red_block_store(v, M + 2, partials);
+}
+
+// zeroth moments of each of the S lattices of natural-layout full populations
+__global__ void __launch_bounds__(RED_BLOCK)
+pops_partials_kernel(const double* __restrict__ in, int S, long long N, double* __restrict__ partials) {
+  double v[RED_MAXV];
+  for (int s = 0; s < RED_MAXV; ++s) v[s] = 0.0;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < N)
+    for (int L = 0; L < S; ++L)
+      for (int i = 0; i < 27; ++i) v[L] += in[((long long)L * 27 + i) * N + n];
+  red_block_store(v, S, partials);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK)
+red_final_kernel(const double* __restrict__ partials, int nblocks, int nv, double* __restrict__ sums) {
+  __shared__ double sh[RED_BLOCK];
+  for (int s = 0; s < nv; ++s) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += RED_BLOCK) t += partials[(long long)b * nv + s];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = RED_BLOCK / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[s] = sh[0];
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -55,7 +139,9 @@ struct lbm_mix {
   const lbm::KernelSet* ks = nullptr;
   lbm::DevParams<double> p64{};
   lbm::DevParams<float> p32{};
-  lbm::CodecParams codec{};
+  double base[(lbm::MAXM + 2) * 27] = {};   // host copy of the reference rest equilibria
+  double* d_base = nullptr;
+  bool has_reference = false;
   void* pops = nullptr;
   size_t pops_bytes = 0;
   void* scratch = nullptr;
@@ -79,7 +165,7 @@ struct lbm_mix {
   lbm::LaunchCtx ctx() {
     lbm::LaunchCtx c;
     c.N = N; c.stream = stream; c.pops = pops; c.side = scratch; c.err = d_err;
-    c.partials = d_partials; c.p64 = &p64; c.p32 = &p32; c.codec = &codec; c.ev = nullptr;
+    c.partials = d_partials; c.p64 = &p64; c.p32 = &p32; c.base = d_base; c.ev = nullptr;
     return c;
   }
   lbm_status fail(lbm_status s, const std::string& m) { err = m; return s; }
@@ -104,6 +190,111 @@ struct lbm_mix {
     if (s != LBM_OK) return s;
     if (flag) return fail(LBM_ERR_NONFINITE, "a node reached non-positive density or temperature (or NaN)");
     return LBM_OK;
+  }
+  // Reference rest state (mass fractions Y, temperature T, density rho):
+  // base tables of every lattice, their sums RL and the derived constants.
+  lbm_status set_reference(const double* Y, double T, double rho) {
+    if (!(T > 0.0) || !(rho > 0.0) || !std::isfinite(T) || !std::isfinite(rho))
+      return fail(LBM_ERR_ARG, "reference state has non-positive temperature or density");
+    lbm::DevParams<double>& d = p64;
+    const int S = M + 2;
+    auto w1 = [](int c, double z) { return c == 0 ? 1.0 - z : 0.5 * z; };
+    auto W = [&](int i, double z) {
+      return w1(lbm::cx_of(i), z) * w1(lbm::cy_of(i), z) * w1(lbm::cz_of(i), z);
+    };
+    double inv_m = 0.0, Cv = 0.0;
+    for (int a = 0; a < M; ++a) { inv_m += Y[a] * d.inv_mass[a]; Cv += Y[a] * d.Cv_a[a]; }
+    const double R = d.R_U * inv_m, th = R * T;
+    for (int a = 0; a < M; ++a)
+      for (int i = 0; i < 27; ++i) base[a * 27 + i] = Y[a] * rho * W(i, d.R_a[a] * T);     // Eq. (27eq) at rest
+    for (int i = 0; i < 27; ++i) base[M * 27 + i] = rho * W(i, th);                      // Eq. (feq) at rest
+    const double rhoE = rho * Cv * T, P = rho * th, Z = 0.5 * (1.0 - 3.0 * th) * P;
+    for (int i = 0; i < 27; ++i) {                                                       // Eq. (gieq) at rest
+      const int c2 = lbm::c2_of(i);
+      const double E = rhoE - 1.5 * P + 0.5 * c2 * rho;
+      const double BZ = c2 == 0 ? 3.0 * Z : (c2 == 1 ? -0.5 * Z : 0.0);
+      base[(M + 1) * 27 + i] = W(i, th) * E + BZ;
+    }
+    for (int L = 0; L < lbm::MAXM + 2; ++L) { d.RL[L] = 0.0; d.scale[L] = 1.0; d.inv_scale[L] = 1.0; }
+    for (int L = 0; L < S; ++L) {
+      double sum = 0.0;
+      for (int i = 0; i < 27; ++i) sum += base[L * 27 + i];
+      d.RL[L] = sum;
+      if (prec == LBM_PREC_FP16_STORE || prec == LBM_PREC_BF16_STORE) {
+        d.scale[L] = 1.0 / std::fabs(sum);
+        d.inv_scale[L] = std::fabs(sum);
+      }
+    }
+    double Rsp = 0.0;
+    for (int a = 0; a < M; ++a) Rsp += d.RL[a];
+    double im = 0.0, cv = 0.0;
+    for (int a = 0; a < lbm::MAXM; ++a) {
+      d.Yr[a] = a < M ? d.RL[a] / Rsp : 0.0;
+      if (a < M) { im += d.Yr[a] * d.inv_mass[a]; cv += d.Yr[a] * d.Cv_a[a]; }
+    }
+    d.Rsp = Rsp;
+    d.Tr = T;
+    d.Rr = d.R_U * im;
+    d.thr = d.Rr * T;
+    d.Pr = d.RL[M] * d.thr;
+    d.Cvr = cv;
+    d.cE = d.RL[M + 1] - d.RL[M] * cv * T;
+    double pix = 0.0;
+    for (int i = 0; i < 27; ++i) pix += base[M * 27 + i] * (double)(lbm::cx_of(i) * lbm::cx_of(i));
+    d.cPi = pix - d.RL[M] * d.thr;
+    d.cS = d.RL[M] - Rsp;
+    fill_params<float>(p32, d);
+    p32.rho_eps = 1e-7f;
+    lbm_status st = cuda(cudaMemcpyAsync(d_base, base, sizeof(double) * S * 27, cudaMemcpyHostToDevice, stream),
+                         "upload reference table");
+    if (st != LBM_OK) return st;
+    st = cuda(cudaStreamSynchronize(stream), "synchronize");
+    if (st == LBM_OK) has_reference = true;
+    return st;
+  }
+  // Host sums of nv reduced values (partials from the kernels above).
+  lbm_status reduce_to_host(int nblocks, int nv, double* out) {
+    red_final_kernel<<<1, RED_BLOCK, 0, stream>>>(d_partials, nblocks, nv, d_sums);
+    lbm_status st = cuda(cudaGetLastError(), "reduction kernel");
+    if (st != LBM_OK) return st;
+    launches += 2;
+    st = cuda(cudaMemcpyAsync(out, d_sums, sizeof(double) * nv, cudaMemcpyDeviceToHost, stream), "copy sums");
+    if (st != LBM_OK) return st;
+    return cuda(cudaStreamSynchronize(stream), "synchronize");
+  }
+  lbm_status reference_from_fields(const double* dX, const double* dT, const double* dP) {
+    const int nb = (int)((N + RED_BLOCK - 1) / RED_BLOCK);
+    field_partials_kernel<<<nb, RED_BLOCK, 0, stream>>>(dX, dT, dP, M, N, d_partials);
+    double sums[RED_MAXV];
+    lbm_status st = reduce_to_host(nb, M + 2, sums);
+    if (st != LBM_OK) return st;
+    double Xm[lbm::MAXM], mbar = 0.0, xs = 0.0;
+    for (int a = 0; a < M; ++a) { Xm[a] = sums[a] / (double)N; xs += Xm[a]; }
+    for (int a = 0; a < M; ++a) { Xm[a] /= xs; mbar += Xm[a] * p64.mass[a]; }
+    const double T = sums[M] / (double)N, P = sums[M + 1] / (double)N;
+    double Y[lbm::MAXM];
+    for (int a = 0; a < M; ++a) Y[a] = Xm[a] * p64.mass[a] / mbar;
+    const double rho = P * mbar / (p64.R_U * T);
+    return set_reference(Y, T, rho);
+  }
+  lbm_status reference_from_pops(const double* dpops) {
+    const int nb = (int)((N + RED_BLOCK - 1) / RED_BLOCK);
+    pops_partials_kernel<<<nb, RED_BLOCK, 0, stream>>>(dpops, M + 2, N, d_partials);
+    double sums[RED_MAXV];
+    lbm_status st = reduce_to_host(nb, M + 2, sums);
+    if (st != LBM_OK) return st;
+    double r[lbm::MAXM], tot = 0.0;
+    for (int a = 0; a < M; ++a) r[a] = sums[a] / (double)N;
+    const double rho = sums[M] / (double)N, rhoE = sums[M + 1] / (double)N;
+    if (!p64.weak) {
+      double others = 0.0;
+      for (int a = 0; a < M; ++a) if (a != p64.slaved) others += r[a];
+      if (rho - others > 0.0) r[p64.slaved] = rho - others;
+    }
+    for (int a = 0; a < M; ++a) tot += r[a];
+    double Y[lbm::MAXM], Cv = 0.0;
+    for (int a = 0; a < M; ++a) { Y[a] = r[a] / tot; Cv += Y[a] * p64.Cv_a[a]; }
+    return set_reference(Y, rhoE / (rho * Cv), rho);
   }
   lbm_status ready() {
     if (!pops || !scratch) return fail(LBM_ERR_STATE, "buffers not bound");
@@ -200,19 +391,11 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   d.rho_eps = 1e-14;
   fill_params<float>(h->p32, d);
   h->p32.rho_eps = 1e-7f;
-  for (int L = 0; L < lbm::MAXS; ++L) {
-    h->codec.scale[L] = 1.0f; h->codec.inv_scale[L] = 1.0f;
-    for (int i = 0; i < 27; ++i) h->codec.base[L][i] = 0.0f;
-  }
-  if (h->prec == LBM_PREC_FP16_STORE || h->prec == LBM_PREC_BF16_STORE) {
-    delete h;
-    g_create_error = "reduced-precision storage is not built yet";
-    return LBM_ERR_UNSUPPORTED;
-  }
 
   const long long nblocks = (h->N + 255) / 256;
   cudaError_t e = cudaMalloc(&h->d_err, 256);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, (size_t)nblocks * (M + 5) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, (size_t)nblocks * 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_base, sizeof(double) * (lbm::MAXM + 2) * 27);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sums, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 256, h->stream);
   if (e != cudaSuccess) {
@@ -220,6 +403,7 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_sums) cudaFree(h->d_sums);
+    if (h->d_base) cudaFree(h->d_base);
     delete h;
     return LBM_ERR_CUDA;
   }
@@ -279,6 +463,7 @@ lbm_status lbm_mix_init_fields(lbm_mix_t h, const double* X, const double* u, co
     dX = st; du = st + M * N; dT = st + (M + 3) * N; dP = st + (M + 4) * N;
   }
   if ((s = h->cuda(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "clear flag")) != LBM_OK) return s;
+  if ((s = h->reference_from_fields(dX, dT, dP)) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->init(h->ctx(), dX, du, dT, dP), "init kernel")) != LBM_OK) return s;
   h->launches += 1;
   h->steps = 0;
@@ -366,6 +551,7 @@ lbm_status lbm_mix_set_populations(lbm_mix_t h, const double* in, int host_ptrs)
       return s;
     src = h->d_stage;
   }
+  if (!h->has_reference && (s = h->reference_from_pops(src)) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->set_pops(h->ctx(), (int)(h->steps & 1), src), "set_populations kernel")) != LBM_OK) return s;
   h->launches += 1;
   h->initialized = true;
@@ -383,7 +569,13 @@ lbm_status lbm_mix_diagnostics(lbm_mix_t h, double* sums) {
   if ((s = h->cuda(cudaMemcpyAsync(sums, h->d_sums, (size_t)(h->M + 5) * sizeof(double), cudaMemcpyDeviceToHost,
                                    h->stream), "device-to-host copy")) != LBM_OK)
     return s;
-  return h->check_flag();
+  s = h->check_flag();
+  // the kernels sum deviations from the reference tables; add the tables' sums
+  const double Nd = (double)h->N;
+  for (int a = 0; a < h->M; ++a) sums[a] += Nd * h->p64.RL[a];
+  sums[h->M] += Nd * h->p64.RL[h->M];
+  sums[h->M + 4] += Nd * h->p64.RL[h->M + 1];
+  return s;
 }
 
 lbm_status lbm_mix_synchronize(lbm_mix_t h) {
@@ -423,7 +615,7 @@ lbm_status lbm_mix_destroy(lbm_mix_t h) {
   cudaStreamSynchronize(h->stream);
   if (h->owns_buffers) { cudaFree(h->pops); cudaFree(h->scratch); }
   if (h->d_stage) cudaFree(h->d_stage);
-  cudaFree(h->d_err); cudaFree(h->d_partials); cudaFree(h->d_sums);
+  cudaFree(h->d_err); cudaFree(h->d_partials); cudaFree(h->d_sums); cudaFree(h->d_base);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return LBM_OK;

@@ -1,14 +1,15 @@
 // lbm_codec.cuh -- storage codec of the populations.
 //
-// FP64 and FP32 storage hold the populations as they are.  The reduced-
-// precision storage types hold a shifted, scaled deviation
-//     d = s_L (f_i - b_{L,i}),   f_i = b_{L,i} + d / s_L,
-// where b_{L,i} is the rest equilibrium of lattice L at a reference state
-// (the product weights of that lattice's temperature times its reference
-// density) and s_L a per-lattice scale; arithmetic is FP32.  The direction
-// index i is always the LOGICAL direction of the population (the AA pattern
-// moves values between slots but never changes their direction).
+// Every lattice L is stored as the deviation d = f - b_L,i of its
+// populations from the rest equilibrium b of a reference state (the
+// host-side table in lbm_api.cu).  FP64 and FP32 storage hold d as it is;
+// the reduced-precision types hold s_L d with a per-lattice scale s_L
+// (1 / the lattice's reference zeroth moment), and the arithmetic is FP32.
+// Deviations are small where the flow is near its reference state, so the
+// rounding of storage is relative to them rather than to f.
 #pragma once
+
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -16,37 +17,27 @@
 
 namespace lbm {
 
-constexpr int MAXS = 10;  // M + 2 <= 10
-
-struct CodecParams {
-  float base[MAXS][27];
-  float scale[MAXS];
-  float inv_scale[MAXS];
-};
-
-template <class Store, class Real>
-__device__ __forceinline__ Real codec_load(const CodecParams& cp, const Store* __restrict__ p,
-                                           long long idx, int L, int i) {
+template <class Store, class Real, class P>
+__device__ __forceinline__ Real codec_load(const P& p, const Store* __restrict__ ptr, long long idx, int L) {
   if constexpr (std::is_same<Store, __half>::value) {
-    return (Real)(cp.base[L][i] + __half2float(p[idx]) * cp.inv_scale[L]);
+    return (Real)(__half2float(ptr[idx]) * p.inv_scale[L]);
   } else if constexpr (std::is_same<Store, __nv_bfloat16>::value) {
-    return (Real)(cp.base[L][i] + __bfloat162float(p[idx]) * cp.inv_scale[L]);
+    return (Real)(__bfloat162float(ptr[idx]) * p.inv_scale[L]);
   } else {
-    (void)cp; (void)L; (void)i;
-    return (Real)p[idx];
+    (void)p; (void)L;
+    return (Real)ptr[idx];
   }
 }
 
-template <class Store, class Real>
-__device__ __forceinline__ void codec_store(const CodecParams& cp, Store* __restrict__ p,
-                                            long long idx, int L, int i, Real v) {
+template <class Store, class Real, class P>
+__device__ __forceinline__ void codec_store(const P& p, Store* __restrict__ ptr, long long idx, int L, Real d) {
   if constexpr (std::is_same<Store, __half>::value) {
-    p[idx] = __float2half_rn(((float)v - cp.base[L][i]) * cp.scale[L]);
+    ptr[idx] = __float2half_rn((float)d * p.scale[L]);
   } else if constexpr (std::is_same<Store, __nv_bfloat16>::value) {
-    p[idx] = __float2bfloat16_rn(((float)v - cp.base[L][i]) * cp.scale[L]);
+    ptr[idx] = __float2bfloat16_rn((float)d * p.scale[L]);
   } else {
-    (void)cp; (void)L; (void)i;
-    p[idx] = (Store)v;
+    (void)p; (void)L;
+    ptr[idx] = (Store)d;
   }
 }
 

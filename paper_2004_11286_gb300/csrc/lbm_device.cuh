@@ -63,6 +63,17 @@ struct DevParams {
   Real phi[MAXM][MAXM];  // Wilke factors, Eq. (wilkePhi)
   Real Cab[MAXM][MAXM];  // 1 / (D_ab m_a m_b): 1/tau_ab = R_U T m Cab (Eq. tauab)
   double Cab64[MAXM][MAXM];
+  // Reference rest state.  Populations are stored as deviations d = f - b
+  // from each lattice's rest equilibrium b at this state; RL[L] = sum_i b_Li.
+  Real RL[MAXM + 2];
+  Real Yr[MAXM];         // reference mass fractions, RL[a] / sum_a RL[a]
+  Real Tr, Rr, thr, Pr;  // reference T, mixture R, theta = R T, P = RL[f] theta
+  Real Cvr;              // reference mixture C_v
+  Real cE;               // RL[g] - RL[f] Cvr Tr       (rounding-level constant)
+  Real cPi;              // sum_i b_fi c_ix^2 - RL[f] thr (rounding-level constant)
+  Real cS;               // RL[f] - sum_a RL[a]
+  Real Rsp;              // sum_a RL[a]
+  Real scale[MAXM + 2], inv_scale[MAXM + 2];   // storage scale of reduced-precision modes
 };
 
 // ---------------------------------------------------------------------------
@@ -128,60 +139,87 @@ __device__ __forceinline__ void aa_write_loc(int parity, const Nbr& nb, long lon
 }
 
 // ---------------------------------------------------------------------------
-// Per-node thermodynamic state (Secs. 2.1, 3.1, 3.3, 3.5).
+// Per-node thermodynamic state (Secs. 2.1, 3.1, 3.3, 3.5), carried as full
+// values plus their deviations from the reference rest state, so that every
+// equilibrium can be formed as a small deviation without cancellation.
 // ---------------------------------------------------------------------------
 template <int M, class Real>
 struct Thermo {
-  Real rho_a[M];      // coupled species densities
+  Real rho_a[M], rho_a_dev[M];   // coupled species densities and deviations from RL[a]
   Real Y[M];
-  Real rho_sp;        // density seen by the species (rho under strong coupling)
-  Real m, R, Cv, Cp, T, P, usq;
-  Real u[3];          // mixture velocity (momentum lattice)
-  Real u_sp[3];       // velocity seen by the species
+  Real rho_sp;                   // density seen by the species (rho under strong coupling)
+  Real rho, rho_dev;             // mixture density (momentum lattice), deviation from RL[f]
+  Real m, R, Cv, Cp, usq;
+  Real T, dT, theta, dtheta, P, dP;
+  Real u[3];                     // mixture velocity (momentum lattice)
+  Real u_sp[3];                  // velocity seen by the species
   Real omega;
 };
 
-// Coupling, composition, caloric closure and omega.  rho_a_raw are the
-// species zeroth moments (the slaved entry is ignored under strong coupling),
-// ja_sum the sum of species momenta (used under weak coupling only).
+// rdev: species zeroth-moment deviations (the slaved entry is ignored under
+// strong coupling); ja_sum: sum of species momenta (weak coupling only);
+// rho_dev, j, rhoE_dev: momentum/energy lattice moments as deviations.
 template <int M, class Real>
-__device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Real (&rho_a_raw)[M],
-                                             const Real (&ja_sum)[3], Real rho, const Real (&j)[3],
-                                             Real rhoE, Thermo<M, Real>& th) {
-  Real inv_rho = Real(1) / rho;
+__device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Real (&rdev)[M],
+                                             const Real (&ja_sum)[3], Real rho_dev, const Real (&j)[3],
+                                             Real rhoE_dev, Thermo<M, Real>& th) {
+  th.rho_dev = rho_dev;
+  th.rho = p.RL[M] + rho_dev;
+  const Real rho = th.rho;
+  const Real inv_rho = Real(1) / rho;
   th.u[0] = j[0] * inv_rho; th.u[1] = j[1] * inv_rho; th.u[2] = j[2] * inv_rho;
+  Real sp_dev;   // rho_sp - Rsp
   if (!p.weak) {
     // Eqs. (rhoMATCH), (uMATCH): the slaved species takes the deficit.
     Real others = Real(0);
 #pragma unroll
-    for (int a = 0; a < M; ++a) if (a != p.slaved) others += rho_a_raw[a];
+    for (int a = 0; a < M; ++a) if (a != p.slaved) others += rdev[a];
 #pragma unroll
-    for (int a = 0; a < M; ++a) th.rho_a[a] = (a == p.slaved) ? rho - others : rho_a_raw[a];
+    for (int a = 0; a < M; ++a) {
+      th.rho_a_dev[a] = (a == p.slaved) ? p.cS + rho_dev - others : rdev[a];
+      th.rho_a[a] = p.RL[a] + th.rho_a_dev[a];
+    }
     th.rho_sp = rho;
+    sp_dev = p.cS + rho_dev;
     th.u_sp[0] = th.u[0]; th.u_sp[1] = th.u[1]; th.u_sp[2] = th.u[2];
   } else {
-    Real s = Real(0);
+    sp_dev = Real(0);
 #pragma unroll
-    for (int a = 0; a < M; ++a) { th.rho_a[a] = rho_a_raw[a]; s += rho_a_raw[a]; }
-    th.rho_sp = s;
-    Real is = Real(1) / s;
+    for (int a = 0; a < M; ++a) {
+      th.rho_a_dev[a] = rdev[a];
+      th.rho_a[a] = p.RL[a] + rdev[a];
+      sp_dev += rdev[a];
+    }
+    th.rho_sp = p.Rsp + sp_dev;
+    const Real is = Real(1) / th.rho_sp;
     th.u_sp[0] = ja_sum[0] * is; th.u_sp[1] = ja_sum[1] * is; th.u_sp[2] = ja_sum[2] * is;
   }
-  Real inv_sp = Real(1) / th.rho_sp;
-  Real inv_m = Real(0), Cv = Real(0), Cp = Real(0);
+  const Real inv_sp = Real(1) / th.rho_sp;
+  Real inv_m = Real(0), d_inv_m = Real(0), Cv = Real(0), dCv = Real(0), Cp = Real(0);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    th.Y[a] = th.rho_a[a] * inv_sp;                      // Eq. (mixtureDensity)
-    inv_m += th.Y[a] * p.inv_mass[a];                    // Eq. (meanMolecularWeight)
-    Cv += th.Y[a] * p.Cv_a[a];                           // Eq. (Cvmix)
+    th.Y[a] = th.rho_a[a] * inv_sp;                               // Eq. (mixtureDensity)
+    const Real dY = (th.rho_a_dev[a] - p.Yr[a] * sp_dev) * inv_sp; // Y_a - Yr_a
+    inv_m += th.Y[a] * p.inv_mass[a];                             // Eq. (meanMolecularWeight)
+    d_inv_m += dY * p.inv_mass[a];
+    Cv += th.Y[a] * p.Cv_a[a];                                    // Eq. (Cvmix)
+    dCv += dY * p.Cv_a[a];
     Cp += th.Y[a] * p.Cp_a[a];
   }
   th.m = Real(1) / inv_m;
-  th.R = p.R_U * inv_m;                                  // Eq. (defineSpecificGasContant)
+  th.R = p.R_U * inv_m;                                           // Eq. (defineSpecificGasContant)
+  const Real dR = p.R_U * d_inv_m;
   th.Cv = Cv; th.Cp = Cp;
   th.usq = th.u[0] * th.u[0] + th.u[1] * th.u[1] + th.u[2] * th.u[2];
-  th.T = (rhoE * inv_rho - Real(0.5) * th.usq) / Cv;    // Eq. (temperature2), T0 = 0
-  th.P = rho * th.R * th.T;                              // Eq. (eosIdealGas)
+  // Eq. (temperature2) with T0 = 0, rho E = rho (C_v T + u^2/2), written for
+  // T - Tr:  rho C_v (T - Tr) = rho E - rho u^2/2 - rho C_v Tr.
+  th.dT = (p.cE + rhoE_dev - Real(0.5) * rho * th.usq - rho_dev * p.Cvr * p.Tr - rho * dCv * p.Tr)
+        / (rho * Cv);
+  th.T = p.Tr + th.dT;
+  th.theta = th.R * th.T;
+  th.dtheta = dR * th.T + p.Rr * th.dT;
+  th.P = rho * th.theta;                                          // Eq. (eosIdealGas)
+  th.dP = rho_dev * th.theta + p.RL[M] * th.dtheta;
   if (p.omega_is_fixed) {
     th.omega = p.omega_fixed;
   } else {
@@ -197,7 +235,7 @@ __device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Rea
       for (int b = 0; b < M; ++b) den += p.phi[a][b] * X[b];
       mu += p.mu[a] * X[a] / den;
     }
-    th.omega = Real(2) * th.P / (th.P + Real(2) * mu);   // Eq. (omega)
+    th.omega = Real(2) * th.P / (th.P + Real(2) * mu);            // Eq. (omega)
   }
 }
 

@@ -7,7 +7,6 @@
 namespace lbm {
 
 template <class Real> struct DevParams;
-struct CodecParams;
 
 struct LaunchCtx {
   long long N;
@@ -18,7 +17,7 @@ struct LaunchCtx {
   double* partials;
   const DevParams<double>* p64;
   const DevParams<float>* p32;
-  const CodecParams* codec;
+  const double* base;   // device table [S][27] of the reference rest equilibria
   cudaEvent_t* ev;   // 4 events bracketing the step's kernels, or nullptr
 };
 
@@ -32,11 +31,17 @@ struct KernelSet {
   int launches_per_step;
 };
 
-// prec: 0 FP64, 1 FP32, 2 FP16 storage, 3 BF16 storage; nullptr if not built.
-const KernelSet* kernel_set_m1(int prec);
-const KernelSet* kernel_set_m2(int prec);
-const KernelSet* kernel_set_m3(int prec);
-const KernelSet* kernel_set_m4(int prec);
-const KernelSet* kernel_set_m8(int prec);
+// One launcher table per (species count, precision); see inst_m*_*.cu.
+#define LBM_DECLARE_SETS(MM)                           \
+  const KernelSet* kernel_set_m##MM##_f64();           \
+  const KernelSet* kernel_set_m##MM##_f32();           \
+  const KernelSet* kernel_set_m##MM##_f16();           \
+  const KernelSet* kernel_set_m##MM##_bf16();
+LBM_DECLARE_SETS(1)
+LBM_DECLARE_SETS(2)
+LBM_DECLARE_SETS(3)
+LBM_DECLARE_SETS(4)
+LBM_DECLARE_SETS(8)
+#undef LBM_DECLARE_SETS
 
 }  // namespace lbm

@@ -1,18 +1,13 @@
-// lbm_inst.cuh -- explicit instantiation of the launcher table for one
-// species count (one translation unit per M keeps builds parallel).
+// lbm_inst.cuh -- explicit instantiation of one launcher table (one species
+// count and one precision per translation unit keeps builds parallel).
 #pragma once
 
 #include "lbm_kernels.cuh"
 
-#define LBM_INSTANTIATE(MM)                                                   \
-  namespace lbm {                                                             \
-  const KernelSet* kernel_set_m##MM(int prec) {                               \
-    static const KernelSet s64 = Launch<MM, double, double>::make();          \
-    static const KernelSet s32 = Launch<MM, float, float>::make();            \
-    switch (prec) {                                                           \
-      case 0: return &s64;                                                    \
-      case 1: return &s32;                                                    \
-      default: return nullptr;                                                \
-    }                                                                         \
-  }                                                                           \
+#define LBM_INSTANTIATE(MM, TAG, REAL, STORE)                                \
+  namespace lbm {                                                            \
+  const KernelSet* kernel_set_m##MM##_##TAG() {                              \
+    static const KernelSet s = Launch<MM, REAL, STORE>::make();              \
+    return &s;                                                               \
+  }                                                                          \
   }

@@ -97,71 +97,157 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// B_i . Z for a vector Z (Eq. Bi): 1 on the rest velocity for every component,
+// -1/2 |c_ia| on the six face velocities, 0 elsewhere.
+template <class Real, int I>
+__device__ __forceinline__ Real BdotZ(const Real (&Z)[3]) {
+  constexpr int k2 = c2_of(I);
+  if constexpr (k2 == 0) return Z[0] + Z[1] + Z[2];
+  else if constexpr (k2 == 1) {
+    constexpr int a = cx_of(I) ? 0 : (cy_of(I) ? 1 : 2);
+    return Real(-0.5) * Z[a];
+  } else {
+    return Real(0);
+  }
+}
+
+// Product of three triplets for velocity I: t_x(c_x) t_y(c_y) t_z(c_z).
+template <class Real, int I>
+__device__ __forceinline__ Real prod3(const Triplet<Real>& tx, const Triplet<Real>& ty, const Triplet<Real>& tz) {
+  return tri(tx, cx_of(I)) * tri(ty, cy_of(I)) * tri(tz, cz_of(I));
+}
+
+// Exact telescoped difference a_x a_y a_z - r_x r_y r_z with da = a - r.
+template <class Real, int I>
+__device__ __forceinline__ Real prod3_diff(const Triplet<Real> (&a)[3], const Triplet<Real> (&r)[3],
+                                           const Triplet<Real> (&da)[3]) {
+  constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+  return tri(da[0], cx) * tri(a[1], cy) * tri(a[2], cz) + tri(r[0], cx) * tri(da[1], cy) * tri(a[2], cz)
+       + tri(r[0], cx) * tri(r[1], cy) * tri(da[2], cz);
+}
+
+// Product-form equilibrium relative to the reference rest state (Sec. 2.4):
+// for velocity xi and zeta = zr + dz, the triplets a = Psi(xi, zeta),
+// r = Psi(0, zr) and their exact difference
+//   da = (-xi^2 - dz, (xi + xi^2 + dz)/2, (-xi + xi^2 + dz)/2).
+template <class Real>
+struct PFDev {
+  Triplet<Real> a[3], r[3], da[3];
+};
+template <class Real>
+__device__ __forceinline__ void pf_dev(PFDev<Real>& P, const Real (&xi)[3], Real zr, Real dz) {
+  const Real z = zr + dz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Real x = xi[c], x2 = x * x;
+    P.r[c].z = Real(1) - zr; P.r[c].p = Real(0.5) * zr; P.r[c].m = P.r[c].p;
+    P.a[c].z = Real(1) - (x2 + z); P.a[c].p = Real(0.5) * (x + x2 + z); P.a[c].m = Real(0.5) * (-x + x2 + z);
+    P.da[c].z = -(x2 + dz); P.da[c].p = Real(0.5) * (x + x2 + dz); P.da[c].m = Real(0.5) * (-x + x2 + dz);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Equilibrium initialisation (Eqs. 27eq, fixed, feq, gieq); natural layout.
+// Equilibrium initialisation (Eqs. 27eq, fixed, feq, gieq), evaluated in FP64
+// as full populations and stored as deviations from the base table.
 // ---------------------------------------------------------------------------
-template <int M, class Real, class Store>
+template <int M, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-init_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict__ pops,
+init_kernel(const DevParams<double> p, Store* __restrict__ pops, const double* __restrict__ base,
             const double* __restrict__ Xin, const double* __restrict__ uin,
             const double* __restrict__ Tin, const double* __restrict__ Pin) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
-  Real X[M], u[3];
+  double X[M], u[3];
 #pragma unroll
-  for (int a = 0; a < M; ++a) X[a] = (Real)Xin[a * N + n];
+  for (int a = 0; a < M; ++a) X[a] = Xin[a * N + n];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) u[c] = (Real)uin[c * N + n];
-  Real T = (Real)Tin[n], P = (Real)Pin[n];
-  Real m = Real(0);
+  for (int c = 0; c < 3; ++c) u[c] = uin[c * N + n];
+  const double T = Tin[n], P = Pin[n];
+  double m = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) m += X[a] * p.mass[a];
-  Real R = p.R_U / m;
-  Real rho = P / (R * T);
-  Real Y[M], Cv = Real(0), Cp = Real(0);
+  const double R = p.R_U / m;
+  const double rho = P / (R * T);
+  double Y[M], Cv = 0.0, Cp = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     Y[a] = X[a] * p.mass[a] / m;
     Cv += Y[a] * p.Cv_a[a];
     Cp += Y[a] * p.Cp_a[a];
   }
-  Real usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  Real rhoE = rho * (Cv * T + Real(0.5) * usq);
+  const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double rhoE = rho * (Cv * T + 0.5 * usq);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    Real ra = Y[a] * rho, ze = p.R_a[a] * T;
-    Triplet<Real> tx = psi_triplet(u[0], ze), ty = psi_triplet(u[1], ze), tz = psi_triplet(u[2], ze);
+    const double ra = Y[a] * rho, ze = p.R_a[a] * T;
+    const Triplet<double> tx = psi_triplet(u[0], ze), ty = psi_triplet(u[1], ze), tz = psi_triplet(u[2], ze);
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      codec_store<Store, Real>(cp, pops, (a * Q + i) * N + n, a, i,
-                               ra * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i)));
+    for (int i = 0; i < Q; ++i) {
+      const double v = ra * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i));
+      codec_store<Store, double>(p, pops, (a * Q + i) * N + n, a, v - base[a * Q + i]);
+    }
   }
   {
-    Real ze = R * T;
-    Triplet<Real> tx = psi_triplet(u[0], ze), ty = psi_triplet(u[1], ze), tz = psi_triplet(u[2], ze);
+    const double ze = R * T;
+    const Triplet<double> tx = psi_triplet(u[0], ze), ty = psi_triplet(u[1], ze), tz = psi_triplet(u[2], ze);
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      codec_store<Store, Real>(cp, pops, (M * Q + i) * N + n, M, i,
-                               rho * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i)));
+    for (int i = 0; i < Q; ++i) {
+      const double v = rho * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i));
+      codec_store<Store, double>(p, pops, (M * Q + i) * N + n, M, v - base[M * Q + i]);
+    }
   }
   {
-    Real theta = R * T, hk = Cp * T + Real(0.5) * usq;
-    Real Mt[6];
+    const double theta = R * T, hk = Cp * T + 0.5 * usq;
+    double Mt[6];
     Mt[0] = hk * (P + rho * u[0] * u[0]) + P * u[0] * u[0];
     Mt[1] = hk * (P + rho * u[1] * u[1]) + P * u[1] * u[1];
     Mt[2] = hk * (P + rho * u[2] * u[2]) + P * u[2] * u[2];
     Mt[3] = hk * rho * u[0] * u[1] + P * u[0] * u[1];
     Mt[4] = hk * rho * u[0] * u[2] + P * u[0] * u[2];
     Mt[5] = hk * rho * u[1] * u[2] + P * u[1] * u[2];
-    GCoef<Real> gc = g_coef(theta, rhoE, Mt);
-    Real mt[3] = {hk * rho * u[0] / theta, hk * rho * u[1] / theta, hk * rho * u[2] / theta};
+    const GCoef<double> gc = g_coef(theta, rhoE, Mt);
+    const double mt[3] = {hk * rho * u[0] / theta, hk * rho * u[1] / theta, hk * rho * u[2] / theta};
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
-      Real w = tri(gc.w, cx_of(i)) * tri(gc.w, cy_of(i)) * tri(gc.w, cz_of(i));
-      Real v = w * (g_even_part<Real, i>(gc) + dotc<Real, i>(mt)) + g_BZ<Real, i>(gc);
-      codec_store<Store, Real>(cp, pops, ((M + 1) * Q + i) * N + n, M + 1, i, v);
+      const double w = tri(gc.w, cx_of(i)) * tri(gc.w, cy_of(i)) * tri(gc.w, cz_of(i));
+      const double v = w * (g_even_part<double, i>(gc) + dotc<double, i>(mt)) + g_BZ<double, i>(gc);
+      codec_store<Store, double>(p, pops, ((M + 1) * Q + i) * N + n, M + 1, v - base[(M + 1) * Q + i]);
     });
+  }
+}
+
+// Zeroth/first moments of the stored deviations needed by the thermodynamic
+// state (Eqs. densitya, auxua, f0momDensity, f1momMomentum, g0momTotalEnergy).
+template <int M, class Real, class Store>
+__device__ __forceinline__ void load_state_moments(const DevParams<Real>& p, const Store* __restrict__ pops,
+                                                   int parity, const Nbr& nb, long long n, bool skip_slaved,
+                                                   Real (&rdev)[M], Real (&ja)[M][3], Real& rho_dev,
+                                                   Real (&j)[3], Real& rhoE_dev) {
+  const long long N = p.N;
+#pragma unroll
+  for (int a = 0; a < M; ++a) { rdev[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
+  rho_dev = Real(0); j[0] = j[1] = j[2] = Real(0); rhoE_dev = Real(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    long long node; int slot;
+    aa_read_loc(parity, nb, n, i, node, slot);
+    const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      if (skip_slaved && a == p.slaved) continue;
+      const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+      rdev[a] += v;
+      if (cx) ja[a][0] += cx * v;
+      if (cy) ja[a][1] += cy * v;
+      if (cz) ja[a][2] += cz * v;
+    }
+    const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M);
+    rho_dev += fv;
+    if (cx) j[0] += cx * fv;
+    if (cy) j[1] += cy * fv;
+    if (cz) j[2] += cz * fv;
+    rhoE_dev += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1);
   }
 }
 
@@ -173,37 +259,23 @@ init_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict__ p
 // ---------------------------------------------------------------------------
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-side_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __restrict__ pops,
-            Real* __restrict__ side, int parity) {
+side_kernel(const DevParams<Real> p, const Store* __restrict__ pops, Real* __restrict__ side, int parity) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
-  Real rho_a[M], jsum[3] = {Real(0), Real(0), Real(0)};
-  Real rho = Real(0), j[3] = {Real(0), Real(0), Real(0)}, rhoE = Real(0);
+  Real rdev[M], ja[M][3], rho_dev, j[3], rhoE_dev;
+  load_state_moments<M, Real, Store>(p, pops, parity, nb, n, !p.weak, rdev, ja, rho_dev, j, rhoE_dev);
+  Real jsum[3] = {Real(0), Real(0), Real(0)};
+  if (p.weak) {
 #pragma unroll
-  for (int a = 0; a < M; ++a) rho_a[a] = Real(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    long long node; int slot;
-    aa_read_loc(parity, nb, n, i, node, slot);
-    const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      if (!p.weak && a == p.slaved) continue;
-      Real v = codec_load<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i);
-      rho_a[a] += v;
-      if (p.weak) { jsum[0] += cx * v; jsum[1] += cy * v; jsum[2] += cz * v; }
-    }
-    Real fv = codec_load<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i);
-    rho += fv; j[0] += cx * fv; j[1] += cy * fv; j[2] += cz * fv;
-    rhoE += codec_load<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i);
+    for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
   }
   Thermo<M, Real> th;
-  thermo_state<M, Real>(p, rho_a, jsum, rho, j, rhoE, th);
-  Real a3 = Real(1) - Real(3) * th.R * th.T;
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
+  const Real a3 = Real(1) - Real(3) * th.theta;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) side[c * N + n] = j[c] * a3 - rho * th.u[c] * th.u[c] * th.u[c];
+  for (int c = 0; c < 3; ++c) side[c * N + n] = j[c] * a3 - th.rho * th.u[c] * th.u[c] * th.u[c];
   side[3 * N + n] = Real(1) / th.omega - Real(0.5);
   side[4 * N + n] = th.Cp;
 }
@@ -233,12 +305,18 @@ grad_kernel(const DevParams<Real> p, Real* __restrict__ side) {
 }
 
 // ---------------------------------------------------------------------------
-// Pass 3: the fused collide + stream of every lattice at one node.
+// Pass 3: the fused collide + stream of every lattice at one node, written
+// for the stored deviations d = f - b of the populations from the reference
+// rest equilibria (the update is affine, so d' = f' - b exactly):
+//   species (Eq. SMlbm):  d' = d + 2 beta_a (e_a - d) + (beta_a - 1) F_a
+//   f (Eq. fwithcorrection): d' = d + omega (e - d) + A_i . X
+//   g (Eq. g):            d' = d + omega (e_g - d) + w_i(theta) c_i . K / theta
+// with e = f^eq - b formed from deviation quantities (no O(f) cancellation).
 // ---------------------------------------------------------------------------
 template <int M, class Real, class Store, int PAR>
 __global__ void __launch_bounds__(BLOCK)
-collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict__ pops,
-               const Real* __restrict__ side, unsigned* __restrict__ err) {
+collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, const Real* __restrict__ side,
+               unsigned* __restrict__ err) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
@@ -251,35 +329,37 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     long long node; int slot;
     aa_read_loc(PAR, nb, n, i, node, slot);
 #pragma unroll
-    for (int a = 0; a < M; ++a) k[a][i] = codec_load<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i);
-    f[i] = codec_load<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i);
-    g[i] = codec_load<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i);
+    for (int a = 0; a < M; ++a) k[a][i] = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+    f[i] = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M);
+    g[i] = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1);
   }
 
-  // a2: moments (Eqs. densitya, auxua, f0momDensity, f1momMomentum, boldP, g0momTotalEnergy, q)
-  Real rho_a[M], ja[M][3];
-  Real rho = Real(0), j[3] = {Real(0), Real(0), Real(0)}, Pi[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
-  Real rhoE = Real(0), q[3] = {Real(0), Real(0), Real(0)};
+  // a2: moments of the deviations (the reference tables have zero first and
+  // off-diagonal second moments)
+  Real rdev[M], ja[M][3];
+  Real rho_dev = Real(0), j[3] = {Real(0), Real(0), Real(0)};
+  Real S[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
+  Real rhoE_dev = Real(0), q[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
-  for (int a = 0; a < M; ++a) { rho_a[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
+  for (int a = 0; a < M; ++a) { rdev[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      rho_a[a] += k[a][i];
+      rdev[a] += k[a][i];
       if (cx) ja[a][0] += cx * k[a][i];
       if (cy) ja[a][1] += cy * k[a][i];
       if (cz) ja[a][2] += cz * k[a][i];
     }
-    rho += f[i];
-    if (cx) { j[0] += cx * f[i]; Pi[0] += f[i]; }
-    if (cy) { j[1] += cy * f[i]; Pi[1] += f[i]; }
-    if (cz) { j[2] += cz * f[i]; Pi[2] += f[i]; }
-    if (cx && cy) Pi[3] += (cx * cy) * f[i];
-    if (cx && cz) Pi[4] += (cx * cz) * f[i];
-    if (cy && cz) Pi[5] += (cy * cz) * f[i];
-    rhoE += g[i];
+    rho_dev += f[i];
+    if (cx) { j[0] += cx * f[i]; S[0] += f[i]; }
+    if (cy) { j[1] += cy * f[i]; S[1] += f[i]; }
+    if (cz) { j[2] += cz * f[i]; S[2] += f[i]; }
+    if (cx && cy) S[3] += (cx * cy) * f[i];
+    if (cx && cz) S[4] += (cx * cz) * f[i];
+    if (cy && cz) S[5] += (cy * cz) * f[i];
+    rhoE_dev += g[i];
     if (cx) q[0] += cx * g[i];
     if (cy) q[1] += cy * g[i];
     if (cz) q[2] += cz * g[i];
@@ -292,7 +372,7 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
   }
   Thermo<M, Real> th;
-  thermo_state<M, Real>(p, rho_a, jsum, rho, j, rhoE, th);
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
   if (!p.weak) {
     // Eq. (uMATCH): slaved species momentum = mixture momentum deficit.
     Real o[3] = {Real(0), Real(0), Real(0)};
@@ -303,6 +383,7 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     for (int a = 0; a < M; ++a)
       if (a == p.slaved) { ja[a][0] = j[0] - o[0]; ja[a][1] = j[1] - o[1]; ja[a][2] = j[2] - o[2]; }
   }
+  const Real rho = th.rho;
   if (!(rho > Real(0)) || !(th.T > Real(0)) || !(th.rho_sp > Real(0))) atomicOr(err, 1u);
   const Real om = th.omega;
   const Real om1 = omega1_of<M, Real>(p, th);
@@ -345,18 +426,17 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     beta[a] = it / (Real(2) + it);                      // dt / (2 tau_a + dt)
   }
 
-  // a7: species collision, Eqs. (SMlbm), (fstar1):
-  //   k' = (1 - 2 beta_a) k + 2 beta_a f^eq_a + (beta_a - 1) F_a,
-  //   F_ai = sum_b kap_ab [Psi_i(u, R_b T) - Psi_i(u + V_b, R_b T)], kap_ab = Y_a rho_b / tau_ab.
-  // The per-axis differences of the triplets are formed exactly:
+  // a7: species.  Equilibrium deviation e_ai = rho_a (Psi_i - W_i) + (rho_a - RL_a) W_i
+  // with W_i the reference weights; F_ai = sum_b kap_ab [Psi_i(u, R_b T) - Psi_i(u + V_b, R_b T)]
+  // (Eq. fstar1), kap_ab = Y_a rho_b / tau_ab, from exact per-axis differences
   //   Psi_0(xi) - Psi_0(xi + V) = V (2 xi + V) = e,  Psi_{+-1}: -e/2 -+ V/2.
-  Triplet<Real> te[M][3], td[M][3];
+  PFDev<Real> sp[M];
+  Triplet<Real> td[M][3];
 #pragma unroll
   for (int b = 0; b < M; ++b) {
-    const Real ze = p.R_a[b] * th.T;
+    pf_dev<Real>(sp[b], th.u_sp, p.R_a[b] * p.Tr, p.R_a[b] * th.dT);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      te[b][c] = psi_triplet(th.u_sp[c], ze);
       const Real v = V[b][c];
       const Real e = v * (Real(2) * th.u_sp[c] + v);
       td[b][c].z = e;
@@ -371,36 +451,51 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     for (int b = 0; b < M; ++b) kap[a][b] = th.Y[a] * th.rho_a[b] * itab[a][b];
 
   // a8: momentum lattice, Eqs. (feq), (fwithcorrection), (Ai).
-  const Real thetaf = th.R * th.T;
-  const Triplet<Real> fx = psi_triplet(th.u[0], thetaf), fy = psi_triplet(th.u[1], thetaf),
-                      fz = psi_triplet(th.u[2], thetaf);
+  PFDev<Real> fp;
+  pf_dev<Real>(fp, th.u, p.thr, th.dtheta);
 
-  // a9: energy lattice.  Since G is affine in its vector argument,
-  //   g' = (1 - omega) g + omega G(q^eq) + w_i c_i . K / theta,
-  //   K = (omega - omega_1)(q^b - q^eq) + omega_1 rho sum_a H_a Y_a V_a
-  //       + (1/2)(2 - omega_1) P sum_a H_a grad Y_a,
-  // which is Eq. (g) with Eqs. (gstareq1mom), (interdiffusion), (corrFourier)
-  // written without the 1/(omega - omega_1) factors.
+  // a9: energy lattice.  With N = R^eq - rho E theta I, Eqs. (geq2mom),
+  // (eosIdealGas) and Mayer give N = P theta I + rho (h + theta) u u
+  // (h = H + u^2/2), so the ansatz of Eqs. (gansatz)-(RcorrectionPrime) reads
+  //   G_i(m) = w_i(theta) [E_i + m . c_i / theta] + B_i . Z,
+  //   E_i = rho E - 3P/2 + rho |c_i|^2 / 2 + Gc ((u . c_i)^2 / theta - u^2),
+  //   Z_a = (1 - 3 theta) P / 2 + (1 - 3 theta) Gc u_a^2,  Gc = rho (h + theta) / (2 theta),
+  // whose deviation from the reference rest state is again a small quantity.
+  // G is affine in m, so Eq. (g) becomes g' = (1 - omega) g + omega G(q^eq)
+  // + w_i c_i . K / theta with K = (omega - omega_1)(q^b - q^eq)
+  // + omega_1 rho sum_a H_a Y_a V_a + (1/2)(2 - omega_1) P sum_a H_a grad Y_a
+  // (Eqs. gstareq1mom, interdiffusion, corrFourier without their 1/(omega - omega_1)).
+  const Real theta = th.theta, thr = p.thr, dth = th.dtheta;
   const Real P = th.P, T = th.T;
   const Real hk = th.Cp * T + Real(0.5) * th.usq;
+  const Real inv_theta = Real(1) / theta;
+  const Real Gc = rho * (hk + theta) * Real(0.5) * inv_theta;
   const Real* u = th.u;
-  Real Peq[6];
-  Peq[0] = P + rho * u[0] * u[0]; Peq[1] = P + rho * u[1] * u[1]; Peq[2] = P + rho * u[2] * u[2];
-  Peq[3] = rho * u[0] * u[1]; Peq[4] = rho * u[0] * u[2]; Peq[5] = rho * u[1] * u[2];
-  Real Mt[6];
+  Triplet<Real> gw, gwr, gdw;
+  gw.z = Real(1) - theta; gw.p = Real(0.5) * theta; gw.m = gw.p;          // Eq. (w0)
+  gwr.z = Real(1) - thr; gwr.p = Real(0.5) * thr; gwr.m = gwr.p;
+  gdw.z = -dth; gdw.p = Real(0.5) * dth; gdw.m = gdw.p;
+  const Real E0 = (p.RL[M + 1] + rhoE_dev) - Real(1.5) * P - Gc * th.usq;
+  const Real dE0 = rhoE_dev - Real(1.5) * th.dP - Gc * th.usq;
+  Real dZ[3];
+  {
+    const Real z1 = Real(1) - Real(3) * theta;
+    const Real zb = Real(0.5) * (z1 * th.dP - Real(3) * dth * p.Pr);
 #pragma unroll
-  for (int s = 0; s < 6; ++s) Mt[s] = hk * Peq[s];
-  Mt[0] += P * u[0] * u[0]; Mt[1] += P * u[1] * u[1]; Mt[2] += P * u[2] * u[2];
-  Mt[3] += P * u[0] * u[1]; Mt[4] += P * u[0] * u[2]; Mt[5] += P * u[1] * u[2];
-  const GCoef<Real> gc = g_coef(thetaf, rhoE, Mt);
-  Real dP[6];
-#pragma unroll
-  for (int s = 0; s < 6; ++s) dP[s] = Pi[s] - Peq[s];
+    for (int c = 0; c < 3; ++c) dZ[c] = zb + z1 * Gc * u[c] * u[c];
+  }
+  Real dP6[6];   // Pi - P^eq from deviations
+  dP6[0] = p.cPi + S[0] - th.dP - rho * u[0] * u[0];
+  dP6[1] = p.cPi + S[1] - th.dP - rho * u[1] * u[1];
+  dP6[2] = p.cPi + S[2] - th.dP - rho * u[2] * u[2];
+  dP6[3] = S[3] - rho * u[0] * u[1];
+  dP6[4] = S[4] - rho * u[0] * u[2];
+  dP6[5] = S[5] - rho * u[1] * u[2];
   Real qeq[3] = {hk * j[0], hk * j[1], hk * j[2]};
   Real qb[3];
-  qb[0] = q[0] - (u[0] * dP[0] + u[1] * dP[3] + u[2] * dP[4]);
-  qb[1] = q[1] - (u[0] * dP[3] + u[1] * dP[1] + u[2] * dP[5]);
-  qb[2] = q[2] - (u[0] * dP[4] + u[1] * dP[5] + u[2] * dP[2]);
+  qb[0] = q[0] - (u[0] * dP6[0] + u[1] * dP6[3] + u[2] * dP6[4]);
+  qb[1] = q[1] - (u[0] * dP6[3] + u[1] * dP6[1] + u[2] * dP6[5]);
+  qb[2] = q[2] - (u[0] * dP6[4] + u[1] * dP6[5] + u[2] * dP6[2]);
   Real hyv[3] = {Real(0), Real(0), Real(0)};
   const Real rY = p.weak ? rho / th.rho_sp : Real(1);   // rho Y_a = rY * rho_a
 #pragma unroll
@@ -410,35 +505,29 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     for (int c = 0; c < 3; ++c) hyv[c] += s * V[a][c];
   }
   const Real c1 = om1 * T * rY, c2 = Real(0.5) * (Real(2) - om1) * P * T, dw = om - om1;
-  const Real inv_theta = Real(1) / thetaf;
   Real mvec[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     mvec[c] = (om * qeq[c] + dw * (qb[c] - qeq[c]) + c1 * hyv[c] + c2 * dCp[c]) * inv_theta;
 
   // a10: collide every direction and store with the AA write addressing.
-  // The rest direction (i = 13) is done last: its equilibria and F_a,13 are
-  // the conservation remainders (rho_a, rho, rho E minus the other 26),
-  // identical to the product forms in exact arithmetic; in finite precision
-  // this keeps the per-step zeroth moments free of the systematic bias that
-  // sum_i w_i(theta) != 1 would otherwise inject every step.
-  const Real one_m_om = Real(1) - om;
-  Real s_keq[M], s_F[M], s_feq = Real(0), s_geq = Real(0);
+  // The rest direction (i = 13) is done last: its equilibrium deviations and
+  // F_a,13 are the conservation remainders, identical to the product forms in
+  // exact arithmetic, so the zeroth moments carry no per-step rounding bias.
+  Real s_e[M], s_F[M], s_f = Real(0), s_g = Real(0);
 #pragma unroll
-  for (int a = 0; a < M; ++a) { s_keq[a] = Real(0); s_F[a] = Real(0); }
+  for (int a = 0; a < M; ++a) { s_e[a] = Real(0); s_F[a] = Real(0); }
   static_for<0, Q>([&](auto I_) {
     constexpr int i = decltype(I_)::value;
     if constexpr (i != 13) {
-      constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
       long long node; int slot;
       aa_write_loc(PAR, nb, n, i, node, slot);
       // species
       Real Dif[M];
 #pragma unroll
       for (int b = 0; b < M; ++b) {
-        const Real ex = tri(te[b][0], cx), ey = tri(te[b][1], cy), ez = tri(te[b][2], cz);
-        const Real dx = tri(td[b][0], cx), dy = tri(td[b][1], cy), dz = tri(td[b][2], cz);
-        // a_x a_y a_z - s_x s_y s_z with s = a - d
+        const Real ex = tri(sp[b].a[0], cx_of(i)), ey = tri(sp[b].a[1], cy_of(i)), ez = tri(sp[b].a[2], cz_of(i));
+        const Real dx = tri(td[b][0], cx_of(i)), dy = tri(td[b][1], cy_of(i)), dz = tri(td[b][2], cz_of(i));
         const Real sx = ex - dx, sy = ey - dy;
         Dif[b] = dx * ey * ez + sx * dy * ez + sx * sy * dz;
       }
@@ -447,26 +536,36 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
         Real F = Real(0);
 #pragma unroll
         for (int b = 0; b < M; ++b) F += kap[a][b] * Dif[b];
-        const Real feq = th.rho_a[a] * tri(te[a][0], cx) * tri(te[a][1], cy) * tri(te[a][2], cz);
-        s_keq[a] += feq; s_F[a] += F;
-        const Real kn = k[a][i] + Real(2) * beta[a] * (feq - k[a][i]) + (beta[a] - Real(1)) * F;
-        codec_store<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i, kn);
+        const Real e = th.rho_a[a] * prod3_diff<Real, i>(sp[a].a, sp[a].r, sp[a].da)
+                     + th.rho_a_dev[a] * prod3<Real, i>(sp[a].r[0], sp[a].r[1], sp[a].r[2]);
+        s_e[a] += e; s_F[a] += F;
+        const Real kn = k[a][i] + Real(2) * beta[a] * (e - k[a][i]) + (beta[a] - Real(1)) * F;
+        codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, kn);
       }
       // momentum lattice
       {
-        const Real feq = rho * tri(fx, cx) * tri(fy, cy) * tri(fz, cz);
-        s_feq += feq;
-        Real fn = one_m_om * f[i] + om * feq;
+        const Real e = rho * prod3_diff<Real, i>(fp.a, fp.r, fp.da)
+                     + rho_dev * prod3<Real, i>(fp.r[0], fp.r[1], fp.r[2]);
+        s_f += e;
+        Real fn = f[i] + om * (e - f[i]);
         if constexpr (c2_of(i) == 1) fn += Real(0.5) * dotc<Real, i>(Xc);
-        codec_store<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i, fn);
+        codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fn);
       }
       // energy lattice
       {
-        const Real w = tri(gc.w, cx) * tri(gc.w, cy) * tri(gc.w, cz);
-        const Real geq = w * g_even_part<Real, i>(gc) + g_BZ<Real, i>(gc);
-        s_geq += geq;
-        const Real gn = one_m_om * g[i] + om * geq + w * dotc<Real, i>(mvec);
-        codec_store<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i, gn);
+        const Real uc = dotc<Real, i>(th.u);
+        const Real cc = Real(0.5) * Real(c2_of(i));
+        const Real Ei = E0 + cc * rho + Gc * uc * uc * inv_theta;
+        const Real dEi = dE0 + cc * rho_dev + Gc * uc * uc * inv_theta;
+        const Real wi = prod3<Real, i>(gw, gw, gw);
+        const Real wri = prod3<Real, i>(gwr, gwr, gwr);
+        const Real dwi = tri(gdw, cx_of(i)) * tri(gw, cy_of(i)) * tri(gw, cz_of(i))
+                       + tri(gwr, cx_of(i)) * tri(gdw, cy_of(i)) * tri(gw, cz_of(i))
+                       + tri(gwr, cx_of(i)) * tri(gwr, cy_of(i)) * tri(gdw, cz_of(i));
+        const Real e = dwi * Ei + wri * dEi + BdotZ<Real, i>(dZ);
+        s_g += e;
+        const Real gn = g[i] + om * (e - g[i]) + wi * dotc<Real, i>(mvec);
+        codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gn);
       }
     }
   });
@@ -476,13 +575,13 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
     aa_write_loc(PAR, nb, n, i, node, slot);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const Real feq = th.rho_a[a] - s_keq[a];
-      const Real kn = k[a][i] + Real(2) * beta[a] * (feq - k[a][i]) - (beta[a] - Real(1)) * s_F[a];
-      codec_store<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i, kn);
+      const Real e = th.rho_a_dev[a] - s_e[a];
+      const Real kn = k[a][i] + Real(2) * beta[a] * (e - k[a][i]) - (beta[a] - Real(1)) * s_F[a];
+      codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, kn);
     }
-    codec_store<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i, one_m_om * f[i] + om * (rho - s_feq));
-    codec_store<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i,
-                             one_m_om * g[i] + om * (rhoE - s_geq));
+    codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, f[i] + om * ((rho_dev - s_f) - f[i]));
+    codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
+                             g[i] + om * ((rhoE_dev - s_g) - g[i]));
   }
 }
 
@@ -491,34 +590,18 @@ collide_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict_
 // ---------------------------------------------------------------------------
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK)
-moments_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __restrict__ pops,
-               int parity, double* __restrict__ out) {
+moments_kernel(const DevParams<Real> p, const Store* __restrict__ pops, int parity, double* __restrict__ out) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
-  Real rho_a[M], ja[M][3], rho = Real(0), j[3] = {Real(0), Real(0), Real(0)}, rhoE = Real(0);
-#pragma unroll
-  for (int a = 0; a < M; ++a) { rho_a[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    long long node; int slot;
-    aa_read_loc(parity, nb, n, i, node, slot);
-    const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      Real v = codec_load<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i);
-      rho_a[a] += v; ja[a][0] += cx * v; ja[a][1] += cy * v; ja[a][2] += cz * v;
-    }
-    Real fv = codec_load<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i);
-    rho += fv; j[0] += cx * fv; j[1] += cy * fv; j[2] += cz * fv;
-    rhoE += codec_load<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i);
-  }
+  Real rdev[M], ja[M][3], rho_dev, j[3], rhoE_dev;
+  load_state_moments<M, Real, Store>(p, pops, parity, nb, n, false, rdev, ja, rho_dev, j, rhoE_dev);
   Real jsum[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
   for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
   Thermo<M, Real> th;
-  thermo_state<M, Real>(p, rho_a, jsum, rho, j, rhoE, th);
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
   if (!p.weak) {
     Real o[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -536,7 +619,7 @@ moments_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __res
     for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
   Real J[M][3];
   sm_solve<M, Real>(p, th, itab, ja, J);
-  out[0 * N + n] = (double)rho;
+  out[0 * N + n] = (double)th.rho;
   out[1 * N + n] = (double)th.u[0];
   out[2 * N + n] = (double)th.u[1];
   out[3 * N + n] = (double)th.u[2];
@@ -553,10 +636,10 @@ moments_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __res
   }
 }
 
-// Natural-layout copy of the logical populations (checkpoint interface).
+// Natural-layout full populations (checkpoint interface): f = b + d.
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-get_pops_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __restrict__ pops,
+get_pops_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const double* __restrict__ base,
                 int parity, double* __restrict__ out) {
   const long long n = gtid();
   if (n >= p.N) return;
@@ -567,13 +650,13 @@ get_pops_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __re
     long long node; int slot;
     aa_read_loc(parity, nb, n, i, node, slot);
     for (int L = 0; L < M + 2; ++L)
-      out[(L * Q + i) * N + n] = (double)codec_load<Store, Real>(cp, pops, (L * Q + slot) * N + node, L, i);
+      out[(L * Q + i) * N + n] = base[L * Q + i] + (double)codec_load<Store, Real>(p, pops, (L * Q + slot) * N + node, L);
   }
 }
 
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-set_pops_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict__ pops,
+set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const double* __restrict__ base,
                 int parity, const double* __restrict__ in) {
   const long long n = gtid();
   if (n >= p.N) return;
@@ -584,13 +667,14 @@ set_pops_kernel(const DevParams<Real> p, const CodecParams cp, Store* __restrict
     long long node; int slot;
     aa_read_loc(parity, nb, n, i, node, slot);
     for (int L = 0; L < M + 2; ++L)
-      codec_store<Store, Real>(cp, pops, (L * Q + slot) * N + node, L, i, (Real)in[(L * Q + i) * N + n]);
+      codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L, (Real)(in[(L * Q + i) * N + n] - base[L * Q + i]));
   }
 }
 
 // ---------------------------------------------------------------------------
-// a12: FP64 conservation sums.  Pass 1: per-block partials (warp shuffles,
-// then shared memory); pass 2: one block sums the partials in a fixed order.
+// a12: FP64 conservation sums of the deviations (the host adds N times the
+// reference zeroth moments).  Pass 1: per-block partials (warp shuffles, then
+// shared memory); pass 2: one block sums the partials in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int DIAG_BLOCK = 256;
 
@@ -602,8 +686,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(DIAG_BLOCK)
-diag_partial_kernel(const DevParams<Real> p, const CodecParams cp, const Store* __restrict__ pops,
-                    int parity, double* __restrict__ partials) {
+diag_partial_kernel(const DevParams<Real> p, const Store* __restrict__ pops, int parity, double* __restrict__ partials) {
   constexpr int NV = M + 5;
   __shared__ double red[DIAG_BLOCK / 32][NV];
   const long long n = gtid();
@@ -618,17 +701,17 @@ diag_partial_kernel(const DevParams<Real> p, const CodecParams cp, const Store* 
       long long node; int slot;
       aa_read_loc(parity, nb, n, i, node, slot);
 #pragma unroll
-      for (int a = 0; a < M; ++a) v[a] += (double)codec_load<Store, Real>(cp, pops, (a * Q + slot) * N + node, a, i);
-      double fv = (double)codec_load<Store, Real>(cp, pops, (M * Q + slot) * N + node, M, i);
+      for (int a = 0; a < M; ++a) v[a] += (double)codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+      const double fv = (double)codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M);
       v[M] += fv;
       v[M + 1] += cx_of(i) * fv; v[M + 2] += cy_of(i) * fv; v[M + 3] += cz_of(i) * fv;
-      v[M + 4] += (double)codec_load<Store, Real>(cp, pops, ((M + 1) * Q + slot) * N + node, M + 1, i);
+      v[M + 4] += (double)codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1);
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < NV; ++s) {
-    double t = warp_sum(v[s]);
+    const double t = warp_sum(v[s]);
     if (lane == 0) red[wid][s] = t;
   }
   __syncthreads();
@@ -668,46 +751,46 @@ struct Launch {
   }
   static cudaError_t init(const LaunchCtx& c, const double* X, const double* u, const double* T,
                           const double* Pr) {
-    init_kernel<M, Real, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        P(c), *c.codec, (Store*)c.pops, X, u, T, Pr);
+    init_kernel<M, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
+        *c.p64, (Store*)c.pops, c.base, X, u, T, Pr);
     return cudaGetLastError();
   }
   static cudaError_t step(const LaunchCtx& c, int parity) {
     Real* side = (Real*)c.side;
     if (c.ev) cudaEventRecord(c.ev[0], c.stream);
     side_kernel<M, Real, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        P(c), *c.codec, (const Store*)c.pops, side, parity);
+        P(c), (const Store*)c.pops, side, parity);
     if (c.ev) cudaEventRecord(c.ev[1], c.stream);
     grad_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[2], c.stream);
     if (parity == 0)
       collide_kernel<M, Real, Store, 0><<<grid_for(c.N, BLOCK), BLOCK, 0, c.stream>>>(
-          P(c), *c.codec, (Store*)c.pops, side, c.err);
+          P(c), (Store*)c.pops, side, c.err);
     else
       collide_kernel<M, Real, Store, 1><<<grid_for(c.N, BLOCK), BLOCK, 0, c.stream>>>(
-          P(c), *c.codec, (Store*)c.pops, side, c.err);
+          P(c), (Store*)c.pops, side, c.err);
     if (c.ev) cudaEventRecord(c.ev[3], c.stream);
     return cudaGetLastError();
   }
   static cudaError_t moments(const LaunchCtx& c, int parity, double* out) {
     moments_kernel<M, Real, Store><<<grid_for(c.N, BLOCK), BLOCK, 0, c.stream>>>(
-        P(c), *c.codec, (const Store*)c.pops, parity, out);
+        P(c), (const Store*)c.pops, parity, out);
     return cudaGetLastError();
   }
   static cudaError_t get_pops(const LaunchCtx& c, int parity, double* out) {
     get_pops_kernel<M, Real, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        P(c), *c.codec, (const Store*)c.pops, parity, out);
+        P(c), (const Store*)c.pops, c.base, parity, out);
     return cudaGetLastError();
   }
   static cudaError_t set_pops(const LaunchCtx& c, int parity, const double* in) {
     set_pops_kernel<M, Real, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        P(c), *c.codec, (Store*)c.pops, parity, in);
+        P(c), (Store*)c.pops, c.base, parity, in);
     return cudaGetLastError();
   }
   static cudaError_t diag(const LaunchCtx& c, int parity, double* d_sums) {
     const unsigned nb = grid_for(c.N, DIAG_BLOCK);
     diag_partial_kernel<M, Real, Store><<<nb, DIAG_BLOCK, 0, c.stream>>>(
-        P(c), *c.codec, (const Store*)c.pops, parity, c.partials);
+        P(c), (const Store*)c.pops, parity, c.partials);
     diag_final_kernel<<<1, DIAG_BLOCK, 0, c.stream>>>(c.partials, (int)nb, M + 5, d_sums);
     return cudaGetLastError();
   }
