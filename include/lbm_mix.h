@@ -168,6 +168,26 @@ LBM_API long long lbm_mix_launch_count(lbm_mix_t h);
 LBM_API lbm_status lbm_mix_enable_kernel_timing(lbm_mix_t h, int enable);
 LBM_API int lbm_mix_kernel_times(lbm_mix_t h, double* ms, long long* counts, int nk);
 
+/* Conservation sums that allocate nothing (the paper has no counterpart: this
+ * is a service of the library).  For callers that cannot call cudaMalloc where
+ * they need the sums -- code whose device memory is owned by a pool or arena,
+ * plugins that are only handed device pointers, or loops in which an
+ * allocation and its implicit synchronisation are not allowed.
+ *   pops   device, natural-layout full populations [M+2][27][N] float64
+ *          (as written by lbm_mix_get_populations to a device buffer)
+ *   sums   device, [M+5] float64 output, same order as lbm_mix_diagnostics
+ *   stream cudaStream_t (NULL = legacy default stream); asynchronous
+ * The reduction's scratch is a file-scope __device__ array of 2^18 doubles
+ * (2 MiB, held by every GPU that loads the library until exit); grids whose
+ * per-block partials do not fit (about 5.1e6 nodes at M = 8, 8.4e6 at M = 3)
+ * are rejected with LBM_ERR_ARG.  The first call on a device takes the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the one array: calls that overlap on
+ * the GPU (different streams, or other host threads) race and must be
+ * serialised by the caller.  Errors are reported by lbm_mix_last_error(NULL). */
+LBM_API lbm_status lbm_mix_conserved_sums_noalloc(const double* pops, int M, int nx, int ny, int nz,
+                                                  double* sums, void* cuda_stream);
+
 /* Releases the handle, its internal block and library-allocated buffers. */
 LBM_API lbm_status lbm_mix_destroy(lbm_mix_t h);
 

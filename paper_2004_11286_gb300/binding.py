@@ -58,6 +58,8 @@ SIGNATURES = {
     "lbm_mix_launch_count": (ct.c_longlong, [ct.c_void_p]),
     "lbm_mix_enable_kernel_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_mix_kernel_times": (ct.c_int, [ct.c_void_p, _DP, ct.POINTER(ct.c_longlong), ct.c_int]),
+    "lbm_mix_conserved_sums_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
+                                                  ct.c_void_p, ct.c_void_p]),
     "lbm_mix_destroy": (ct.c_int, [ct.c_void_p]),
     "lbm_mix_last_error": (ct.c_char_p, [ct.c_void_p]),
 }
@@ -257,6 +259,23 @@ class LbmMix:
             self.close()
         except Exception:
             pass
+
+
+def conserved_sums_noalloc(pops, M: int, shape, sums, stream=None):
+    """Conservation sums of device populations [M+2][27][N] into the device
+    tensor ``sums`` [M+5] without any allocation (static scratch in the
+    library).  Both tensors are CUDA float64 and contiguous."""
+    import torch
+    lib = load_library()
+    nz, ny, nx = shape
+    for t in (pops, sums):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("pops and sums must be contiguous CUDA float64 tensors")
+    st = stream if stream is not None else torch.cuda.current_stream(pops.device)
+    rc = lib.lbm_mix_conserved_sums_noalloc(ct.c_void_p(pops.data_ptr()), int(M), int(nx), int(ny), int(nz),
+                                            ct.c_void_p(sums.data_ptr()), ct.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise LbmError(rc, lib.lbm_mix_last_error(None).decode())
 
 
 def from_workload(wl, precision: str = "fp32", **kw) -> LbmMix:

@@ -132,6 +132,9 @@ red_final_kernel(const double* __restrict__ partials, int nblocks, int nv, doubl
 
 }  // namespace
 
+// Message reported by lbm_mix_last_error(NULL) for calls without a handle.
+void lbm_set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct lbm_mix {
   int M = 0, prec = 0, device = 0;
   long long N = 0;
