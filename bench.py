@@ -184,16 +184,17 @@ def _recorded_traffic(kernel: str, precision: str, M: int, nodes: int):
     return float(e["bytes_per_node"]) * nodes
 
 
-def _algorithmic_bytes(M: int, precision: str, slaved_skipped: bool = True):
+def _algorithmic_bytes(M: int, precision: str):
     """Per-node algorithmic bytes of each kernel and of the whole step."""
     b = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
     bs = 8 if precision == "fp64" else 4
     S = M + 2
-    read_side = (S - (1 if slaved_skipped else 0)) * 27 * b
     return {
-        "side_fields": read_side + 5 * bs,          # moments of the non-slaved lattices -> 5 side fields
-        "grad_G": 4 * bs + 3 * bs,                  # Phi, c_omega -> G
-        "collide_stream": 2 * 27 * S * b + 4 * bs,  # every population read + written, G and C_p read
+        # every population read + written once; the senders' deferred terms
+        # (X, K, theta) read once per node; this node's 7 side fields written
+        "collide_stream": 2 * 27 * S * b + 7 * bs + 7 * bs,
+        "grad_GK": 7 * bs + 7 * bs,                 # Phi, c_omega, C_p, s, theta -> G, K, theta
+        "grad_X": 3 * bs + 3 * bs,                  # G -> X
         "step": 2 * 27 * S * b + 2 * 5 * bs,        # method minimum: populations once + side fields once
     }
 

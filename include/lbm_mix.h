@@ -84,7 +84,7 @@ typedef struct {
   double omega_fixed;         /* > 0: constant omega instead of Eq. (omega) */
   double omega1_fixed;        /* > 0: constant omega_1 instead of Eq. (omega1) */
   double R_U;                 /* universal gas constant in lattice units (> 0) */
-  int nx, ny, nz;             /* grid, each >= 1 */
+  int nx, ny, nz;             /* grid, each >= 1, fewer than 2^31 nodes */
   int bc[6];                  /* -x,+x,-y,+y,-z,+z; only LBM_BC_PERIODIC */
   int slaved_species;         /* strong coupling: slaved index, -1 -> M-1 (Sec. 3.5.2) */
   int precision;              /* LBM_PREC_* */
@@ -104,8 +104,11 @@ typedef struct lbm_mix* lbm_mix_t;
 LBM_API lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t* out);
 
 /* Bytes the caller must provide for the populations (S*27*N elements of the
- * storage type) and the scratch side fields (8*N reals: Phi_alpha, 1/omega-1/2,
- * C_p and G_alpha of Eq. Xalpha). */
+ * storage type) and the scratch side fields (17*N reals, FP64 in FP64 mode,
+ * FP32 otherwise: Phi_alpha, 1/omega-1/2, C_p, the q^corr scale and theta
+ * written by each collision; G_alpha, K_alpha and the sender's theta; X_alpha
+ * of Eq. Xalpha).  The scratch also carries the previous step's non-local
+ * terms, which the next step applies to the arriving populations. */
 LBM_API lbm_status lbm_mix_required_bytes(lbm_mix_t h, size_t* pops_bytes, size_t* scratch_bytes);
 
 /* Binds caller-owned device buffers (at least the required sizes, 256-byte
@@ -160,8 +163,8 @@ LBM_API long long lbm_mix_step_count(lbm_mix_t h);
 LBM_API long long lbm_mix_launch_count(lbm_mix_t h);
 
 /* Instrumentation.  With timing enabled, every step records CUDA events on
- * the handle's stream around each of its kernels (index 0: side fields,
- * 1: G_alpha, 2: collide + stream).  lbm_mix_kernel_times synchronises, adds
+ * the handle's stream around each of its kernels (index 0: collide + stream,
+ * 1: G_alpha and K_alpha stencil, 2: X_alpha stencil).  lbm_mix_kernel_times synchronises, adds
  * the elapsed times (ms) of all steps recorded since the previous query into
  * ms[0..nk-1], writes the number of launches per kernel into counts, and
  * forgets them.  Returns the number of kernels per step (3). */

@@ -227,7 +227,7 @@ class LbmMix:
     def synchronize(self):
         self._check(self.lib.lbm_mix_synchronize(self.h))
 
-    KERNEL_NAMES = ("side_fields", "grad_G", "collide_stream")
+    KERNEL_NAMES = ("collide_stream", "grad_GK", "grad_X")
 
     def enable_kernel_timing(self, on: bool = True):
         self._check(self.lib.lbm_mix_enable_kernel_timing(self.h, int(bool(on))))

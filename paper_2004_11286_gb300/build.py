@@ -46,7 +46,10 @@ def _digest(extra_flags) -> str:
 
 
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> Path:
-    """Compile and link ``liblbm_mix.so``; returns its path."""
+    """Compile and link ``liblbm_mix.so``; returns its path.  Additional nvcc
+    flags (tuning macros such as -DLBM_COLLIDE_MINB=3) may also come from the
+    environment variable LBM_NVCC_EXTRA."""
+    extra_flags = list(extra_flags) + os.environ.get("LBM_NVCC_EXTRA", "").split()
     BUILD.mkdir(exist_ok=True)
     stamp = BUILD / "liblbm_mix.stamp"
     digest = _digest(extra_flags)

@@ -299,6 +299,12 @@ struct lbm_mix {
     for (int a = 0; a < M; ++a) { Y[a] = r[a] / tot; Cv += Y[a] * p64.Cv_a[a]; }
     return set_reference(Y, rhoE / (rho * Cv), rho);
   }
+  // No deferred non-local terms are pending for a state set from outside.
+  lbm_status clear_pending() {
+    const size_t es = side_elem_bytes(prec);
+    return cuda(cudaMemsetAsync((char*)scratch + (size_t)lbm::SP_K * N * es, 0,
+                                (size_t)(lbm::NSIDE - lbm::SP_K) * N * es, stream), "clear deferred terms");
+  }
   lbm_status ready() {
     if (!pops || !scratch) return fail(LBM_ERR_STATE, "buffers not bound");
     return LBM_OK;
@@ -318,6 +324,7 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   if (M < 1 || M > lbm::MAXM) return bad("M must be in 1..8");
   if (!p->molar_mass || !p->cv_molar || !p->D) return bad("molar_mass, cv_molar and D are required");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("grid dimensions must be >= 1");
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return bad("grids must have fewer than 2^31 nodes");
   if (!(p->R_U > 0.0)) return bad("R_U must be > 0");
   for (int s = 0; s < 6; ++s)
     if (p->bc[s] != LBM_BC_PERIODIC) { g_create_error = "only periodic boundaries are built"; return LBM_ERR_UNSUPPORTED; }
@@ -467,6 +474,7 @@ lbm_status lbm_mix_init_fields(lbm_mix_t h, const double* X, const double* u, co
   }
   if ((s = h->cuda(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "clear flag")) != LBM_OK) return s;
   if ((s = h->reference_from_fields(dX, dT, dP)) != LBM_OK) return s;
+  if ((s = h->clear_pending()) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->init(h->ctx(), dX, du, dT, dP), "init kernel")) != LBM_OK) return s;
   h->launches += 1;
   h->steps = 0;
@@ -555,6 +563,7 @@ lbm_status lbm_mix_set_populations(lbm_mix_t h, const double* in, int host_ptrs)
     src = h->d_stage;
   }
   if (!h->has_reference && (s = h->reference_from_pops(src)) != LBM_OK) return s;
+  if ((s = h->clear_pending()) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->set_pops(h->ctx(), (int)(h->steps & 1), src), "set_populations kernel")) != LBM_OK) return s;
   h->launches += 1;
   h->initialized = true;

@@ -1,0 +1,346 @@
+// lbm_collide.cuh -- the fused collide + stream of every lattice at one node.
+//
+// Written for the stored deviations d = f - b of the populations from the
+// reference rest equilibria (the update is affine, so d' = f' - b exactly):
+//   species (Eq. SMlbm):     d' = d + 2 beta_a (e_a - d) + (beta_a - 1) F_a
+//   f (Eq. fwithcorrection): d' = d + omega (e - d)         [+ A_i . X, deferred]
+//   g (Eq. g):               d' = d + omega (e_g - d) + w_i(theta) c_i . K / theta
+// with every equilibrium deviation e = f^eq - b formed from deviation
+// quantities (no O(f) cancellation).  The node also writes its side fields
+// for the stencil passes of lbm_stencil.cuh.
+#pragma once
+
+#include "lbm_stencil.cuh"
+
+namespace lbm {
+
+// Threads per block: the deviations of all S lattices are staged in shared
+// memory (S * 27 values per thread), kept near 110 KB per block.
+template <int M, class Real>
+constexpr int collide_block() {
+  constexpr long long per = (long long)(M + 2) * 27 * sizeof(Real);
+  return per * 128 <= 113 * 1024 ? 128 : (per * 64 <= 113 * 1024 ? 64 : 32);
+}
+
+// Minimum resident blocks per SM asked of the register allocator, capped by
+// what the shared-memory tile allows.  3 (168 registers per thread for
+// 128-thread blocks) measured best on GB300 for the 128^3 M = 2 FP32
+// workload: 3570 MLUPS against 3245 (1), 3246 (2) and 2956 (4).
+#ifndef LBM_COLLIDE_MINB
+#define LBM_COLLIDE_MINB 3
+#endif
+template <int M, class Real>
+constexpr int collide_min_blocks() {
+  constexpr long long bytes = (long long)(M + 2) * 27 * sizeof(Real) * collide_block<M, Real>();
+  constexpr long long nb = (227LL * 1024) / bytes;
+  constexpr int fit = nb >= 4 ? 4 : (nb < 1 ? 1 : (int)nb);
+  return LBM_COLLIDE_MINB < fit ? LBM_COLLIDE_MINB : fit;
+}
+
+template <int M, class Real>
+constexpr size_t collide_smem() {
+  return (size_t)(M + 2) * Q * collide_block<M, Real>() * sizeof(Real);
+}
+
+template <int M, class Real, class Store, int PAR>
+__global__ void __launch_bounds__(collide_block<M, Real>(), collide_min_blocks<M, Real>())
+collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
+               unsigned* __restrict__ err) {
+  constexpr int BS = collide_block<M, Real>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);     // [(M+2)*27][BS], thread-private columns
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  const int tid = threadIdx.x;
+  const Nbr nb = make_nbr(p, n);
+
+  // a1 + a2: load (AA addressing), add the deferred terms of the previous
+  // step, accumulate the moments of the deviations (the reference tables have
+  // zero first and off-diagonal second moments) and stage the values.
+  Real rdev[M], ja[M][3];
+  Real rho_dev = Real(0), j[3] = {Real(0), Real(0), Real(0)};
+  Real S[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
+  Real rhoE_dev = Real(0), q[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int a = 0; a < M; ++a) { rdev[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
+  static_for<0, Q>([&](auto I_) {
+    constexpr int i = decltype(I_)::value;
+    constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+    long long node; int slot;
+    aa_read_loc(PAR, nb, n, i, node, slot);
+    Real cf = Real(0), cg = Real(0);
+    if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx, -cy, -cz), cf, cg);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+      sm[(a * Q + i) * BS + tid] = v;
+      rdev[a] += v;
+      if (cx) ja[a][0] += cx * v;
+      if (cy) ja[a][1] += cy * v;
+      if (cz) ja[a][2] += cz * v;
+    }
+    const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+    sm[(M * Q + i) * BS + tid] = fv;
+    rho_dev += fv;
+    if (cx) { j[0] += cx * fv; S[0] += fv; }
+    if (cy) { j[1] += cy * fv; S[1] += fv; }
+    if (cz) { j[2] += cz * fv; S[2] += fv; }
+    if (cx && cy) S[3] += (cx * cy) * fv;
+    if (cx && cz) S[4] += (cx * cz) * fv;
+    if (cy && cz) S[5] += (cy * cz) * fv;
+    const Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+    sm[((M + 1) * Q + i) * BS + tid] = gv;
+    rhoE_dev += gv;
+    if (cx) q[0] += cx * gv;
+    if (cy) q[1] += cy * gv;
+    if (cz) q[2] += cz * gv;
+  });
+
+  // a3: coupling + thermodynamics
+  Real jsum[3] = {Real(0), Real(0), Real(0)};
+  if (p.weak) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
+  }
+  Thermo<M, Real> th;
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
+  if (!p.weak) {
+    // Eq. (uMATCH): slaved species momentum = mixture momentum deficit.
+    Real o[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a != p.slaved) { o[0] += ja[a][0]; o[1] += ja[a][1]; o[2] += ja[a][2]; }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a == p.slaved) { ja[a][0] = j[0] - o[0]; ja[a][1] = j[1] - o[1]; ja[a][2] = j[2] - o[2]; }
+  }
+  const Real rho = th.rho;
+  if (!(rho > Real(0)) || !(th.T > Real(0)) || !(th.rho_sp > Real(0))) atomicOr(err, 1u);
+  const Real om = th.omega;
+  const Real om1 = omega1_of<M, Real>(p, th);
+  const Real P = th.P, T = th.T;
+
+  // a5: this node's side fields: Phi_alpha = j_alpha (1 - 3RT) - rho u_alpha^3 and
+  // c_omega = 1/omega - 1/2 (Eq. Xalpha); C_p and s = (1/2)(2 - omega_1) P T / theta
+  // (sum_a H_a grad Y_a = T grad C_p for constant specific heats, Eq. corrFourier).
+  {
+    const Real a3 = Real(1) - Real(3) * th.theta;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) side[(SP_PHI + c) * N + n] = j[c] * a3 - rho * th.u[c] * th.u[c] * th.u[c];
+    side[SP_COM * N + n] = Real(1) / om - Real(0.5);
+    side[SP_CP * N + n] = th.Cp;
+    side[SP_S * N + n] = Real(0.5) * (Real(2) - om1) * P * T / th.theta;
+    side[SP_TH * N + n] = th.theta;
+  }
+
+  // a4, a6: relaxation times (Eqs. tauab, tau) and the Stefan-Maxwell fluxes.
+  Real itab[M][M];
+  const Real tm = p.R_U * th.T * th.m;
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
+  Real J[M][3];
+  sm_solve<M, Real>(p, th, itab, ja, J);
+  Real V[M][3], beta[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    const bool ok = th.rho_a[a] > p.rho_eps * th.rho_sp;
+    const Real ir = ok ? Real(1) / th.rho_a[a] : Real(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) V[a][c] = J[a][c] * ir;
+    Real it = Real(0);
+#pragma unroll
+    for (int b = 0; b < M; ++b) it += itab[a][b] * th.Y[b];
+    beta[a] = it / (Real(2) + it);                      // dt / (2 tau_a + dt)
+  }
+
+  // The stores run in three phases (f, g, species).  Each starts from an
+  // opaque copy of the neighbour table so that the 26 neighbour addresses are
+  // recomputed there rather than held live since the load phase.  The rest
+  // direction (i = 13) of every lattice goes last: its equilibrium deviation
+  // (and F_a,13) is the conservation remainder, identical to the product form
+  // in exact arithmetic, so the zeroth moments carry no per-step rounding bias.
+
+  // a8: momentum lattice, Eqs. (feq), (fwithcorrection), (Ai):
+  //   e_i = rho (Psi_i(u, theta) - W_i) + (rho - RL_f) W_i,  W_i = Psi_i(0, theta_r).
+  {
+    Real s_f = Real(0);
+    const Real x2[3] = {th.u[0] * th.u[0], th.u[1] * th.u[1], th.u[2] * th.u[2]};
+    const Nbr nbw = opaque(nb);
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      if constexpr (i != 13) {
+        long long node; int slot;
+        aa_write_loc(PAR, nbw, n, i, node, slot);
+        const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
+        s_f += e;
+        const Real fv = sm[(M * Q + i) * BS + tid];
+        codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * (e - fv));
+      }
+    });
+    long long node; int slot;
+    aa_write_loc(PAR, nbw, n, 13, node, slot);
+    const Real fv = sm[(M * Q + 13) * BS + tid];
+    codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
+  }
+
+  // a9: energy lattice.  With N = R^eq - rho E theta I, Eqs. (geq2mom),
+  // (eosIdealGas) and Mayer give N = P theta I + rho (h + theta) u u
+  // (h = H + u^2/2), so the ansatz of Eqs. (gansatz)-(RcorrectionPrime) reads
+  //   G_i(m) = w_i(theta) [E_i + m . c_i / theta] + B_i . Z,
+  //   E_i = rho E - 3P/2 + rho |c_i|^2 / 2 + Gc ((u . c_i)^2 / theta - u^2),
+  //   Z_a = (1 - 3 theta) P / 2 + (1 - 3 theta) Gc u_a^2,  Gc = rho (h + theta) / (2 theta),
+  // whose deviation from the reference rest state is again small.  G is
+  // affine in m, so Eq. (g) becomes g' = (1 - omega) g + omega G(q^eq)
+  // + w_i c_i . K / theta with K = (omega - omega_1)(q^b - q^eq)
+  // + omega_1 rho sum_a H_a Y_a V_a + (1/2)(2 - omega_1) P sum_a H_a grad Y_a
+  // (Eqs. gstareq1mom, interdiffusion, corrFourier without their
+  // 1/(omega - omega_1)); the last, non-local term is deferred.
+  {
+    const Real theta = th.theta, thr = p.thr, dth = th.dtheta;
+    const Real hk = th.Cp * T + Real(0.5) * th.usq;
+    const Real inv_theta = Real(1) / theta;
+    const Real Gc = rho * (hk + theta) * Real(0.5) * inv_theta;
+    const Real* u = th.u;
+    const Real E0 = (p.RL[M + 1] + rhoE_dev) - Real(1.5) * P - Gc * th.usq;
+    const Real dE0 = rhoE_dev - Real(1.5) * th.dP - Gc * th.usq;
+    Real dZ[3];
+    {
+      const Real z1 = Real(1) - Real(3) * theta;
+      const Real zb = Real(0.5) * (z1 * th.dP - Real(3) * dth * p.Pr);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dZ[c] = zb + z1 * Gc * u[c] * u[c];
+    }
+    Real mvec[3];
+    {
+      Real dP6[6];   // Pi - P^eq from deviations
+      dP6[0] = p.cPi + S[0] - th.dP - rho * u[0] * u[0];
+      dP6[1] = p.cPi + S[1] - th.dP - rho * u[1] * u[1];
+      dP6[2] = p.cPi + S[2] - th.dP - rho * u[2] * u[2];
+      dP6[3] = S[3] - rho * u[0] * u[1];
+      dP6[4] = S[4] - rho * u[0] * u[2];
+      dP6[5] = S[5] - rho * u[1] * u[2];
+      const Real qeq[3] = {hk * j[0], hk * j[1], hk * j[2]};
+      Real qb[3];
+      qb[0] = q[0] - (u[0] * dP6[0] + u[1] * dP6[3] + u[2] * dP6[4]);
+      qb[1] = q[1] - (u[0] * dP6[3] + u[1] * dP6[1] + u[2] * dP6[5]);
+      qb[2] = q[2] - (u[0] * dP6[4] + u[1] * dP6[5] + u[2] * dP6[2]);
+      Real hyv[3] = {Real(0), Real(0), Real(0)};
+      const Real rY = p.weak ? rho / th.rho_sp : Real(1);   // rho Y_a = rY * rho_a
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        const Real sv = p.Cp_a[a] * th.rho_a[a];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hyv[c] += sv * V[a][c];
+      }
+      const Real c1 = om1 * T * rY, dw = om - om1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mvec[c] = (om * qeq[c] + dw * (qb[c] - qeq[c]) + c1 * hyv[c]) * inv_theta;
+    }
+    const Real w0 = Real(1) - theta, w1 = Real(0.5) * theta;          // Eq. (w0)
+    const Real r0 = Real(1) - thr, r1 = Real(0.5) * thr;
+    const Real d0 = -dth, d1 = Real(0.5) * dth;
+    Real s_g = Real(0);
+    const Nbr nbw = opaque(nb);
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      if constexpr (i != 13) {
+        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        long long node; int slot;
+        aa_write_loc(PAR, nbw, n, i, node, slot);
+        const Real uc = dotc<Real, i>(th.u);
+        const Real cc = Real(0.5) * Real(c2_of(i));
+        const Real ucu = Gc * uc * uc * inv_theta;
+        const Real Ei = E0 + cc * rho + ucu;
+        const Real dEi = dE0 + cc * rho_dev + ucu;
+        const Real wx = cx ? w1 : w0, wy = cy ? w1 : w0, wz = cz ? w1 : w0;
+        const Real rx = cx ? r1 : r0, ry = cy ? r1 : r0, rz = cz ? r1 : r0;
+        const Real dx = cx ? d1 : d0, dy = cy ? d1 : d0, dz = cz ? d1 : d0;
+        const Real wi = wx * wy * wz;
+        const Real dwi = dx * wy * wz + rx * dy * wz + rx * ry * dz;
+        const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
+        s_g += e;
+        const Real gv = sm[((M + 1) * Q + i) * BS + tid];
+        codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
+                                 gv + om * (e - gv) + wi * dotc<Real, i>(mvec));
+      }
+    });
+    long long node; int slot;
+    aa_write_loc(PAR, nbw, n, 13, node, slot);
+    const Real gv = sm[((M + 1) * Q + 13) * BS + tid];
+    codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
+  }
+
+  // a7: species, Eqs. (SMlbm), (fstar1).  Equilibrium deviation
+  //   e_ai = rho_a (Psi_i(u, R_a T) - W_ai) + (rho_a - RL_a) W_ai,
+  // F_ai = sum_b kap_ab [Psi_i(u, R_b T) - Psi_i(u + V_b, R_b T)], kap_ab = Y_a rho_b / tau_ab,
+  // the bracket from exact per-axis differences
+  //   Psi_0(xi) - Psi_0(xi + V) = V (2 xi + V) = v,  Psi_{+-1}: -v/2 -+ V/2.
+  {
+    const Real x2[3] = {th.u_sp[0] * th.u_sp[0], th.u_sp[1] * th.u_sp[1], th.u_sp[2] * th.u_sp[2]};
+    Real zr[M], dz[M], ev[M][3];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      zr[b] = p.R_a[b] * p.Tr;
+      dz[b] = p.R_a[b] * th.dT;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ev[b][c] = V[b][c] * (Real(2) * th.u_sp[c] + V[b][c]);
+    }
+    Real kap[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int b = 0; b < M; ++b) kap[a][b] = th.Y[a] * th.rho_a[b] * itab[a][b];
+    Real s_e[M], s_F[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) { s_e[a] = Real(0); s_F[a] = Real(0); }
+    const Nbr nbw = opaque(nb);
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      if constexpr (i != 13) {
+        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        long long node; int slot;
+        aa_write_loc(PAR, nbw, n, i, node, slot);
+        Real Dif[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          // a = Psi(u), s = Psi(u + V) per axis; Dif = a_x a_y a_z - s_x s_y s_z
+          const Real z = zr[b] + dz[b];
+          const Real ax = pf_a<Real>(cx, th.u_sp[0], x2[0], z);
+          const Real ay = pf_a<Real>(cy, th.u_sp[1], x2[1], z);
+          const Real az = pf_a<Real>(cz, th.u_sp[2], x2[2], z);
+          const Real tx = pf_v<Real>(cx, V[b][0], ev[b][0]);
+          const Real ty = pf_v<Real>(cy, V[b][1], ev[b][1]);
+          const Real tz = pf_v<Real>(cz, V[b][2], ev[b][2]);
+          const Real sx = ax - tx, sy = ay - ty;
+          Dif[b] = tx * ay * az + sx * ty * az + sx * sy * tz;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          Real F = Real(0);
+#pragma unroll
+          for (int b = 0; b < M; ++b) F += kap[a][b] * Dif[b];
+          const Real e = th.rho_a[a] * pf_diff<Real, i>(th.u_sp, x2, zr[a], dz[a])
+                       + th.rho_a_dev[a] * pf_ref<Real, i>(zr[a]);
+          s_e[a] += e; s_F[a] += F;
+          const Real kv = sm[(a * Q + i) * BS + tid];
+          codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
+                                   kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
+        }
+      }
+    });
+    long long node; int slot;
+    aa_write_loc(PAR, nbw, n, 13, node, slot);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const Real e = th.rho_a_dev[a] - s_e[a];
+      const Real kv = sm[(a * Q + 13) * BS + tid];
+      codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
+                               kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
+    }
+  }
+}
+
+}  // namespace lbm

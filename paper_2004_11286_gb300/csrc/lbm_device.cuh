@@ -16,7 +16,12 @@ namespace lbm {
 
 constexpr int Q = 27;
 constexpr int MAXM = 8;
-constexpr int NSIDE = 8;   // side-field planes: Phi_x,Phi_y,Phi_z, c_omega, C_p, G_x,G_y,G_z
+// Scratch planes per node (Real):
+//   written by collide:  Phi_x,Phi_y,Phi_z (0-2), c_omega (3), C_p (4), s = c2/theta (5), theta (6)
+//   written by grad_GK:  G_x,G_y,G_z (7-9), K_x,K_y,K_z (10-12), theta of the sender (13)
+//   written by grad_X:   X_x,X_y,X_z (14-16)
+constexpr int NSIDE = 17;
+enum SidePlane { SP_PHI = 0, SP_COM = 3, SP_CP = 4, SP_S = 5, SP_TH = 6, SP_G = 7, SP_K = 10, SP_THR = 13, SP_X = 14 };
 
 // Velocity i = (cx+1) + 3(cy+1) + 9(cz+1), Eq. (d3q27vel).
 __host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
@@ -101,24 +106,40 @@ __device__ __forceinline__ Real tri(const Triplet<Real>& t, int c) {
 // Grid addressing.
 // ---------------------------------------------------------------------------
 struct Nbr {
-  long long xs[3], ys[3], zs[3];  // wrapped coordinates for offsets -1, 0, +1 (y,z pre-scaled)
+  unsigned xs[3], ys[3], zs[3];  // wrapped coordinates for offsets -1, 0, +1 (y, z pre-scaled); N < 2^31
   __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
-    return zs[dz + 1] + ys[dy + 1] + xs[dx + 1];
+    return (long long)(zs[dz + 1] + ys[dy + 1] + xs[dx + 1]);
   }
 };
 
 template <class Real>
-__device__ __forceinline__ Nbr make_nbr(const DevParams<Real>& p, long long n) {
+__device__ __forceinline__ Nbr make_nbr(const DevParams<Real>& p, long long n_) {
   Nbr b;
-  long long nx = p.nx, ny = p.ny, nz = p.nz;
-  long long x = n % nx;
-  long long t = n / nx;
-  long long y = t % ny;
-  long long z = t / ny;
+  const unsigned n = (unsigned)n_;
+  const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
+  const unsigned x = n % nx;
+  const unsigned t = n / nx;
+  const unsigned y = t % ny;
+  const unsigned z = t / ny;
+  const unsigned pl = nx * ny;
   b.xs[0] = x == 0 ? nx - 1 : x - 1;  b.xs[1] = x;  b.xs[2] = x == nx - 1 ? 0 : x + 1;
   b.ys[0] = (y == 0 ? ny - 1 : y - 1) * nx;  b.ys[1] = y * nx;  b.ys[2] = (y == ny - 1 ? 0 : y + 1) * nx;
-  b.zs[0] = (z == 0 ? nz - 1 : z - 1) * nx * ny;  b.zs[1] = z * nx * ny;
-  b.zs[2] = (z == nz - 1 ? 0 : z + 1) * nx * ny;
+  b.zs[0] = (z == 0 ? nz - 1 : z - 1) * pl;  b.zs[1] = z * pl;
+  b.zs[2] = (z == nz - 1 ? 0 : z + 1) * pl;
+  return b;
+}
+
+// A copy of the neighbour table that the compiler cannot identify with the
+// original, so addresses recomputed from it are not merged with (and kept
+// live from) those of an earlier phase of the same kernel.
+__device__ __forceinline__ Nbr opaque(const Nbr& a) {
+  Nbr b;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    asm volatile("mov.u32 %0, %1;" : "=r"(b.xs[k]) : "r"(a.xs[k]));
+    asm volatile("mov.u32 %0, %1;" : "=r"(b.ys[k]) : "r"(a.ys[k]));
+    asm volatile("mov.u32 %0, %1;" : "=r"(b.zs[k]) : "r"(a.zs[k]));
+  }
   return b;
 }
 

@@ -1,0 +1,103 @@
+// lbm_readers.cuh -- kernels that read or replace the state between steps:
+// observables (get_moments) and natural-layout copies (checkpoint interface).
+// Readers add the pending deferred terms of the last step, so what they see
+// is the exact post-streaming state.
+#pragma once
+
+#include "lbm_stencil.cuh"
+
+namespace lbm {
+
+// Observables: rho, u, T, P, X_a, Y_a, V_a (Sec. 2.1, Eq. temperature2, Eq. transform12).
+template <int M, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK)
+moments_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const Real* __restrict__ side,
+               int parity, double* __restrict__ out) {
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  const Nbr nb = make_nbr(p, n);
+  Real rdev[M], ja[M][3], rho_dev, j[3], rhoE_dev;
+  load_state_moments<M, Real, Store>(p, pops, side, parity, nb, n, rdev, ja, rho_dev, j, rhoE_dev);
+  Real jsum[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
+  Thermo<M, Real> th;
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
+  if (!p.weak) {
+    Real o[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a != p.slaved) { o[0] += ja[a][0]; o[1] += ja[a][1]; o[2] += ja[a][2]; }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a == p.slaved) { ja[a][0] = j[0] - o[0]; ja[a][1] = j[1] - o[1]; ja[a][2] = j[2] - o[2]; }
+  }
+  Real itab[M][M];
+  const Real tm = p.R_U * th.T * th.m;
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
+  Real J[M][3];
+  sm_solve<M, Real>(p, th, itab, ja, J);
+  out[0 * N + n] = (double)th.rho;
+  out[1 * N + n] = (double)th.u[0];
+  out[2 * N + n] = (double)th.u[1];
+  out[3 * N + n] = (double)th.u[2];
+  out[4 * N + n] = (double)th.T;
+  out[5 * N + n] = (double)th.P;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    out[(6 + a) * N + n] = (double)(th.m * th.Y[a] * p.inv_mass[a]);
+    out[(6 + M + a) * N + n] = (double)th.Y[a];
+    const bool ok = th.rho_a[a] > p.rho_eps * th.rho_sp;
+    const Real ir = ok ? Real(1) / th.rho_a[a] : Real(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[(6 + 2 * M + 3 * a + c) * N + n] = (double)(J[a][c] * ir);
+  }
+}
+
+// Natural-layout full populations: f = b + d (+ the pending deferred term).
+template <int M, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+get_pops_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const Real* __restrict__ side,
+                const double* __restrict__ base, int parity, double* __restrict__ out) {
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  const Nbr nb = make_nbr(p, n);
+  static_for<0, Q>([&](auto I_) {
+    constexpr int i = decltype(I_)::value;
+    long long node; int slot;
+    aa_read_loc(parity, nb, n, i, node, slot);
+    Real cf = Real(0), cg = Real(0);
+    if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cf, cg);
+    for (int L = 0; L < M + 2; ++L) {
+      double v = (double)codec_load<Store, Real>(p, pops, (L * Q + slot) * N + node, L);
+      if (L == M) v += (double)cf;
+      if (L == M + 1) v += (double)cg;
+      out[(L * Q + i) * N + n] = base[L * Q + i] + v;
+    }
+  });
+}
+
+// Replaces the state by natural-layout full populations (no terms pending).
+template <int M, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const double* __restrict__ base,
+                int parity, const double* __restrict__ in) {
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  const Nbr nb = make_nbr(p, n);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    long long node; int slot;
+    aa_read_loc(parity, nb, n, i, node, slot);
+    for (int L = 0; L < M + 2; ++L)
+      codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L, (Real)(in[(L * Q + i) * N + n] - base[L * Q + i]));
+  }
+}
+
+}  // namespace lbm
