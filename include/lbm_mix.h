@@ -89,10 +89,17 @@ typedef struct {
   int slaved_species;         /* strong coupling: slaved index, -1 -> M-1 (Sec. 3.5.2) */
   int precision;              /* LBM_PREC_* */
   int coupling;               /* LBM_COUPLE_* */
-  int closure;                /* LBM_CLOSURE_* (only EXACT in this build) */
+  int closure;                /* LBM_CLOSURE_EXACT, or LBM_CLOSURE_MLP: the learned
+                                 network proposes the fluxes of Eq. (transform12)
+                                 and the exact solve runs where its residual
+                                 exceeds closure_residual_bound (FP32-arithmetic
+                                 precisions with M >= 2 only) */
   double fp64_cond_bound;     /* FP32 paths: solve the M x M system of Eq. (transform12)
                                  in FP64 where its 1-norm condition bound exceeds this
                                  (<= 0 -> 1e3) */
+  double closure_residual_bound; /* LBM_CLOSURE_MLP: largest accepted
+                                 max_{a,c} |(A J~ - r/s)_{a,c}| of the J-form system
+                                 in units of s = max|r| (<= 0 -> 1e-2) */
 } lbm_mix_params;
 
 typedef struct lbm_mix* lbm_mix_t;
@@ -190,6 +197,125 @@ LBM_API int lbm_mix_kernel_times(lbm_mix_t h, double* ms, long long* counts, int
  * serialised by the caller.  Errors are reported by lbm_mix_last_error(NULL). */
 LBM_API lbm_status lbm_mix_conserved_sums_noalloc(const double* pops, int M, int nx, int ny, int nz,
                                                   double* sums, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned Stefan-Maxwell closure.  A network (two hidden layers of width 128
+ * with the exact GELU, a linear output layer) stands in for the per-node
+ * solve of Eq. (transform12) written for the fluxes J_a = rho_a V_a:
+ *   J_a + (1/2) sum_{b!=a} (1/tau_ab)(Y_b J_a - Y_a J_b) = r_a = j_a - rho_a u.
+ * Interface (per node, FP32, row-major [rows][F] / [rows][O]):
+ *   s = max_{a,c} |r_a,c|;
+ *   features, F = pad16(4M + M(M-1)/2 + 1): X_a (a < M); r_a,c / s at
+ *     M + 3a + c; h_ab / (1 + h_ab) for a < b in lexicographic order with
+ *     h_ab = (1/2)(1/tau_ab)(Y_a + Y_b); the constant 1; zeros;
+ *   outputs, O = pad16(3M): J_a,c / s - J0_a,c at 3a + c (the rest unused),
+ *     the correction to the one-sweep Jacobi estimate J0_a,c = (r_a,c / s) / A_aa
+ *     with A the matrix of the system above; the accepted fluxes are
+ *     s (J0 + output).
+ * Weights (FP32, packed): W1 [128][F], b1 [128], W2 [128][128], b2 [128],
+ * W3 [O][128], b3 [O].  The handle owns an FP32 master copy (trained by the
+ * training kernels) and a bf16 image that the tensor-core inference uses
+ * (tcgen05, FP32 accumulation), in lbm_mix_closure_forward and, with
+ * LBM_CLOSURE_MLP, fused into every step.  A new handle starts with zero
+ * weights: the closure is then the Jacobi estimate alone, accepted only
+ * where it meets the bound.  All pointers below are device pointers unless
+ * stated.
+ * ------------------------------------------------------------------------ */
+
+/* F, O and the packed weight count for M species; LBM_ERR_UNSUPPORTED for a
+ * species count without kernels. */
+LBM_API lbm_status lbm_mix_closure_sizes(int M, int* F, int* O, int* n_weights);
+
+/* Replace the FP32 master weights (host_ptr != 0: `w` is host memory,
+ * synchronous) and rebuild the bf16 image; resets the Adam state. */
+LBM_API lbm_status lbm_mix_closure_set_weights(lbm_mix_t h, const float* w, int host_ptr);
+
+/* Copy the FP32 master weights out (host_ptr != 0: host memory, synchronous). */
+LBM_API lbm_status lbm_mix_closure_get_weights(lbm_mix_t h, float* w, int host_ptr);
+
+/* Training pairs at every node of the current state: features [N][F] and
+ * the exact outputs [N][O] (the J-form system solved in FP64, minus the
+ * Jacobi estimate), in the node order of the fields.  Stream-ordered. */
+LBM_API lbm_status lbm_mix_closure_samples(lbm_mix_t h, float* features, float* targets);
+
+/* Network outputs [n][O] for features [n][F] on the tensor cores with the
+ * bf16 image (the arithmetic of the fused inference).  Stream-ordered. */
+LBM_API lbm_status lbm_mix_closure_forward(lbm_mix_t h, const float* features, float* outputs, long long n);
+
+/* Mean-squared loss over the n samples and the 3M valid outputs, and its
+ * gradient with respect to the FP32 master weights (packed like them) from
+ * the FP32 training kernels.  `grad` may be NULL; *loss (host) is written
+ * after a synchronisation. */
+LBM_API lbm_status lbm_mix_closure_loss_grad(lbm_mix_t h, const float* features, const float* targets,
+                                             long long n, float* grad, double* loss);
+
+/* `steps` Adam updates (Kingma & Ba 2015; beta 0.9/0.999, eps 1e-8, rate lr)
+ * of the master weights on consecutive mini-batches of `batch` samples taken
+ * in order (cyclically) from the n pairs; rebuilds the bf16 image.  The caller
+ * shuffles the pairs.  *last_loss (host, may be NULL) is the loss of the last
+ * mini-batch, before its update; the call synchronises. */
+LBM_API lbm_status lbm_mix_closure_train(lbm_mix_t h, const float* features, const float* targets, long long n,
+                                         int batch, int steps, double lr, double* last_loss);
+
+/* Nodes whose network fluxes passed the residual check and nodes that took
+ * the exact solve, summed over the steps since the last reset (host values;
+ * synchronises).  reset != 0 zeroes the counters after reading. */
+LBM_API lbm_status lbm_mix_closure_stats(lbm_mix_t h, long long* accepted, long long* fallback, int reset);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent periodic domains (uneven grids, each
+ * with its own species constants, diffusivities and initial state) stepped
+ * together, one launch per kernel for all of them.  Persistent blocks walk a
+ * list of tiles (domain, first node); the launch shapes come from
+ * lbm_mix_batch_autotune (or lbm_mix_batch_set_config), and pairs of steps
+ * (both AA parities) replay as one captured CUDA graph.  Per node the work
+ * is exactly that of lbm_mix_step.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_mix_batch* lbm_mix_batch_t;
+
+/* `ndomains` parameter blocks (all with the same M, precision and coupling,
+ * the exact closure).  The library allocates one population and one scratch
+ * buffer for all domains and a non-blocking internal stream; every call is
+ * ordered after the work on `cuda_stream`, and the caller's stream waits for
+ * the batched step.  Errors: lbm_mix_last_error(NULL). */
+LBM_API lbm_status lbm_mix_batch_create(const lbm_mix_params* params, int ndomains, void* cuda_stream,
+                                        lbm_mix_batch_t* out);
+
+/* Borrowed handle of domain d for init_fields / set_populations,
+ * get_moments, get_populations and diagnostics (not for step, bind or
+ * destroy: the batch owns it). */
+LBM_API lbm_status lbm_mix_batch_domain(lbm_mix_batch_t b, int d, lbm_mix_t* h);
+
+/* Total nodes over the domains (-1 for NULL). */
+LBM_API long long lbm_mix_batch_nodes(lbm_mix_batch_t b);
+
+/* nsteps steps of every domain (all must be initialised and at the same
+ * step count).  Asynchronous on the caller's stream. */
+LBM_API lbm_status lbm_mix_batch_step(lbm_mix_batch_t b, int nsteps);
+
+/* Times the candidate launch shapes (collide grid: one block per tile or 1-4
+ * blocks per SM, persistent; stencil blocks of 128 or 256 threads, one per
+ * tile or 8/16 per SM) on `trial_steps` steps each, keeps the fastest and
+ * restores the state it started from.  config (may be NULL) receives
+ * [collide grid, stencil block, stencil grid]; *best_ms the step time. */
+LBM_API lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* config, double* best_ms);
+
+/* Sets the launch shapes by hand; use_graph = 0 launches every step. */
+LBM_API lbm_status lbm_mix_batch_set_config(lbm_mix_batch_t b, int grid_collide, int block_stencil,
+                                            int grid_stencil, int use_graph);
+
+/* config[8]: collide grid, stencil block, stencil grid, graphs on, collide
+ * tiles, 128-thread tiles, 256-thread tiles, nodes per collide tile. */
+LBM_API lbm_status lbm_mix_batch_config(lbm_mix_batch_t b, int* config);
+
+/* Waits for the batch and reports a non-physical node (LBM_ERR_NONFINITE). */
+LBM_API lbm_status lbm_mix_batch_synchronize(lbm_mix_batch_t b);
+
+/* Releases the domains, the shared buffers and the graph. */
+LBM_API lbm_status lbm_mix_batch_destroy(lbm_mix_batch_t b);
+
+/* Message of the last error on `b` (of the last failed create if NULL). */
+LBM_API const char* lbm_mix_batch_last_error(lbm_mix_batch_t b);
 
 /* Releases the handle, its internal block and library-allocated buffers. */
 LBM_API lbm_status lbm_mix_destroy(lbm_mix_t h);

@@ -37,6 +37,7 @@ class lbm_mix_params(ct.Structure):
         ("slaved_species", ct.c_int), ("precision", ct.c_int), ("coupling", ct.c_int),
         ("closure", ct.c_int),
         ("fp64_cond_bound", ct.c_double),
+        ("closure_residual_bound", ct.c_double),
     ]
 
 
@@ -60,6 +61,28 @@ SIGNATURES = {
     "lbm_mix_kernel_times": (ct.c_int, [ct.c_void_p, _DP, ct.POINTER(ct.c_longlong), ct.c_int]),
     "lbm_mix_conserved_sums_noalloc": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                                   ct.c_void_p, ct.c_void_p]),
+    "lbm_mix_closure_sizes": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                         ct.POINTER(ct.c_int)]),
+    "lbm_mix_closure_set_weights": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_closure_get_weights": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "lbm_mix_closure_samples": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "lbm_mix_closure_forward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_longlong]),
+    "lbm_mix_closure_loss_grad": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_longlong,
+                                             ct.c_void_p, _DP]),
+    "lbm_mix_closure_train": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_longlong, ct.c_int,
+                                         ct.c_int, ct.c_double, _DP]),
+    "lbm_mix_closure_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong),
+                                         ct.c_int]),
+    "lbm_mix_batch_create": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "lbm_mix_batch_domain": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "lbm_mix_batch_nodes": (ct.c_longlong, [ct.c_void_p]),
+    "lbm_mix_batch_step": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "lbm_mix_batch_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), _DP]),
+    "lbm_mix_batch_set_config": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int]),
+    "lbm_mix_batch_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "lbm_mix_batch_synchronize": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_batch_destroy": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_batch_last_error": (ct.c_char_p, [ct.c_void_p]),
     "lbm_mix_destroy": (ct.c_int, [ct.c_void_p]),
     "lbm_mix_last_error": (ct.c_char_p, [ct.c_void_p]),
 }
@@ -97,6 +120,35 @@ def _dp(a: Optional[np.ndarray]):
     return a.ctypes.data_as(_DP)
 
 
+def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), precision: str = "fp32",
+                coupling: str = "strong", slaved: int = -1, omega_fixed: float = 0.0, omega1_fixed: float = 0.0,
+                R_U: float = 1.0, fp64_cond_bound: float = 0.0, closure: str = "exact",
+                closure_bound: float = 0.0):
+    """(lbm_mix_params, keepalive arrays) for one periodic nz x ny x nx domain."""
+    M = int(len(molar_mass))
+    nz, ny, nx = (int(v) for v in shape)
+    keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in (molar_mass, cv_molar, D)]
+    mu_a = None if mu is None else np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    lam_a = None if lam is None else np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+    keep += [mu_a, lam_a]
+    p = lbm_mix_params()
+    p.M = M
+    p.molar_mass, p.cv_molar, p.D = (_dp(a) for a in keep[:3])
+    p.mu = _dp(mu_a)
+    p.lambda_ = _dp(lam_a)
+    p.omega_fixed, p.omega1_fixed, p.R_U = float(omega_fixed), float(omega1_fixed), float(R_U)
+    p.nx, p.ny, p.nz = nx, ny, nz
+    for k in range(6):
+        p.bc[k] = 0
+    p.slaved_species = int(slaved)
+    p.precision = PREC[precision]
+    p.coupling = COUPLING[coupling]
+    p.closure = CLOSURE[closure]
+    p.fp64_cond_bound = float(fp64_cond_bound)
+    p.closure_residual_bound = float(closure_bound)
+    return p, keep
+
+
 class LbmMix:
     """One simulation handle: a periodic nz x ny x nx grid of M species + f + g.
 
@@ -107,7 +159,8 @@ class LbmMix:
     def __init__(self, molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1),
                  precision: str = "fp32", coupling: str = "strong", slaved: int = -1,
                  omega_fixed: float = 0.0, omega1_fixed: float = 0.0, R_U: float = 1.0,
-                 fp64_cond_bound: float = 0.0, closure: str = "exact", device=None, stream=None):
+                 fp64_cond_bound: float = 0.0, closure: str = "exact", closure_bound: float = 0.0,
+                 device=None, stream=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -116,25 +169,11 @@ class LbmMix:
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
         self.N = nx * ny * nz
-        self._keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
-                      for v in (molar_mass, cv_molar, D)]
-        mu_a = None if mu is None else np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
-        lam_a = None if lam is None else np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
-        self._keep += [mu_a, lam_a]
-        p = lbm_mix_params()
-        p.M = self.M
-        p.molar_mass, p.cv_molar, p.D = (_dp(a) for a in self._keep[:3])
-        p.mu = _dp(mu_a)
-        p.lambda_ = _dp(lam_a)
-        p.omega_fixed, p.omega1_fixed, p.R_U = float(omega_fixed), float(omega1_fixed), float(R_U)
-        p.nx, p.ny, p.nz = nx, ny, nz
-        for s in range(6):
-            p.bc[s] = 0
-        p.slaved_species = int(slaved)
-        p.precision = PREC[precision]
-        p.coupling = COUPLING[coupling]
-        p.closure = CLOSURE[closure]
-        p.fp64_cond_bound = float(fp64_cond_bound)
+        p, self._keep = make_params(molar_mass, cv_molar, D, mu=mu, lam=lam, shape=shape, precision=precision,
+                                    coupling=coupling, slaved=slaved, omega_fixed=omega_fixed,
+                                    omega1_fixed=omega1_fixed, R_U=R_U, fp64_cond_bound=fp64_cond_bound,
+                                    closure=closure, closure_bound=closure_bound)
+        self._owned = True
         self.precision = precision
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -241,6 +280,81 @@ class LbmMix:
             raise LbmError(3, "kernel_times failed")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_NAMES)}
 
+    # -- learned closure -----------------------------------------------------
+    def closure_sizes(self):
+        """(F, O, number of packed FP32 weights) of this handle's network."""
+        return closure_sizes(self.M)
+
+    def _f32(self, t, n: int):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError("expected a contiguous CUDA float32 tensor of %d elements" % n)
+        return ct.c_void_p(t.data_ptr())
+
+    def set_closure_weights(self, w):
+        """FP32 master weights (packed; NumPy host array or CUDA tensor)."""
+        torch = self._torch
+        nw = self.closure_sizes()[2]
+        if isinstance(w, torch.Tensor) and w.is_cuda:
+            self._check(self.lib.lbm_mix_closure_set_weights(self.h, self._f32(w, nw), 0))
+        else:
+            a = np.ascontiguousarray(np.asarray(w, dtype=np.float32).ravel())
+            if a.size != nw:
+                raise ValueError("expected %d weights" % nw)
+            self._check(self.lib.lbm_mix_closure_set_weights(self.h, ct.c_void_p(a.ctypes.data), 1))
+
+    def closure_weights(self) -> np.ndarray:
+        w = np.empty(self.closure_sizes()[2], dtype=np.float32)
+        self._check(self.lib.lbm_mix_closure_get_weights(self.h, ct.c_void_p(w.ctypes.data), 1))
+        return w
+
+    def closure_samples(self):
+        """(features [N, F], exact normalised targets [N, O]) as CUDA float32 tensors."""
+        torch = self._torch
+        F, O, _ = self.closure_sizes()
+        feat = torch.empty((self.N, F), dtype=torch.float32, device=self.device)
+        tgt = torch.empty((self.N, O), dtype=torch.float32, device=self.device)
+        self._check(self.lib.lbm_mix_closure_samples(self.h, ct.c_void_p(feat.data_ptr()),
+                                                     ct.c_void_p(tgt.data_ptr())))
+        return feat, tgt
+
+    def closure_forward(self, feat):
+        """Tensor-core network outputs [n, O] for CUDA float32 features [n, F]."""
+        torch = self._torch
+        F, O, _ = self.closure_sizes()
+        n = feat.shape[0]
+        out = torch.empty((n, O), dtype=torch.float32, device=self.device)
+        self._check(self.lib.lbm_mix_closure_forward(self.h, self._f32(feat, n * F),
+                                                     ct.c_void_p(out.data_ptr()), n))
+        return out
+
+    def closure_loss_grad(self, feat, tgt):
+        """(loss, gradient [n_weights] CUDA float32) from the FP32 training kernels."""
+        torch = self._torch
+        F, O, nw = self.closure_sizes()
+        n = feat.shape[0]
+        g = torch.empty(nw, dtype=torch.float32, device=self.device)
+        loss = ct.c_double()
+        self._check(self.lib.lbm_mix_closure_loss_grad(self.h, self._f32(feat, n * F), self._f32(tgt, n * O), n,
+                                                       ct.c_void_p(g.data_ptr()), ct.byref(loss)))
+        return loss.value, g
+
+    def closure_train(self, feat, tgt, batch: int, steps: int, lr: float) -> float:
+        """Adam steps on the (already shuffled) pairs; returns the last mini-batch loss."""
+        F, O, _ = self.closure_sizes()
+        n = feat.shape[0]
+        loss = ct.c_double()
+        self._check(self.lib.lbm_mix_closure_train(self.h, self._f32(feat, n * F), self._f32(tgt, n * O), n,
+                                                   int(batch), int(steps), float(lr), ct.byref(loss)))
+        return loss.value
+
+    def closure_stats(self, reset: bool = False):
+        """(accepted, fallback) node counts of the network closure."""
+        a, f = ct.c_longlong(), ct.c_longlong()
+        self._check(self.lib.lbm_mix_closure_stats(self.h, ct.byref(a), ct.byref(f), int(bool(reset))))
+        return a.value, f.value
+
     @property
     def step_count(self) -> int:
         return int(self.lib.lbm_mix_step_count(self.h))
@@ -249,16 +363,132 @@ class LbmMix:
     def launch_count(self) -> int:
         return int(self.lib.lbm_mix_launch_count(self.h))
 
+    @classmethod
+    def _borrowed(cls, lib, h, M, shape, precision, device, stream):
+        """Wrapper of a handle owned by a batch (never destroyed here)."""
+        import torch
+        self = cls.__new__(cls)
+        self._torch, self.lib, self.h = torch, lib, h
+        self.M, self.shape = int(M), tuple(int(v) for v in shape)
+        self.N = int(np.prod(self.shape))
+        self.precision, self.device, self.stream = precision, device, stream
+        self._owned = False
+        return self
+
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self.lib.lbm_mix_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+class LbmBatch:
+    """An ensemble of independent periodic domains stepped together.
+
+    ``domains`` is a list of keyword dicts for :func:`make_params` (each with
+    its own constants and shape; all share M, precision and coupling).
+    ``self.domain(d)`` gives an :class:`LbmMix` view of domain d for
+    init_fields, moments, populations and diagnostics."""
+
+    def __init__(self, domains, device=None, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        nd = len(domains)
+        arr = (lbm_mix_params * nd)()
+        self._keep = []
+        self._meta = []
+        for d, kw in enumerate(domains):
+            p, keep = make_params(**kw)
+            arr[d] = p
+            self._keep.append(keep)
+            self._meta.append((len(kw["molar_mass"]), tuple(kw["shape"]), kw.get("precision", "fp32")))
+        self._params = arr
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            b = ct.c_void_p()
+            st = self.lib.lbm_mix_batch_create(ct.cast(arr, ct.c_void_p), nd, ct.c_void_p(self.stream.cuda_stream),
+                                               ct.byref(b))
+            if st != 0:
+                raise LbmError(st, self.lib.lbm_mix_last_error(None).decode())
+        self.b = b
+        self.nd = nd
+        self._views = []
+        for d in range(nd):
+            h = ct.c_void_p()
+            self._check(self.lib.lbm_mix_batch_domain(self.b, d, ct.byref(h)))
+            M, shape, prec = self._meta[d]
+            self._views.append(LbmMix._borrowed(self.lib, h, M, shape, prec, self.device, self.stream))
+
+    def _check(self, st: int):
+        if st != 0:
+            raise LbmError(st, self.lib.lbm_mix_batch_last_error(self.b).decode())
+
+    def domain(self, d: int) -> LbmMix:
+        return self._views[d]
+
+    @property
+    def nodes(self) -> int:
+        return int(self.lib.lbm_mix_batch_nodes(self.b))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbm_mix_batch_step(self.b, int(n)))
+
+    def autotune(self, trial_steps: int = 3):
+        cfg = (ct.c_int * 3)()
+        ms = ct.c_double()
+        self._check(self.lib.lbm_mix_batch_autotune(self.b, int(trial_steps), cfg, ct.byref(ms)))
+        return dict(grid_collide=cfg[0], block_stencil=cfg[1], grid_stencil=cfg[2], ms_per_step=ms.value)
+
+    def set_config(self, grid_collide: int, block_stencil: int, grid_stencil: int, use_graph: bool = True):
+        self._check(self.lib.lbm_mix_batch_set_config(self.b, int(grid_collide), int(block_stencil),
+                                                      int(grid_stencil), int(bool(use_graph))))
+
+    def config(self):
+        c = (ct.c_int * 8)()
+        self._check(self.lib.lbm_mix_batch_config(self.b, c))
+        keys = ("grid_collide", "block_stencil", "grid_stencil", "use_graph", "tiles_collide", "tiles_128",
+                "tiles_256", "collide_block")
+        return dict(zip(keys, list(c)))
+
+    def synchronize(self):
+        self._check(self.lib.lbm_mix_batch_synchronize(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self._views:
+                v.h = None
+            self.lib.lbm_mix_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workload_params(wl, precision: str = "fp32", **kw):
+    """make_params keywords for a ``workloads.Workload``."""
+    params = wl.params()
+    return dict(molar_mass=params["molar_mass"], cv_molar=params["cv_molar"], D=params["D"], mu=params["mu"],
+                lam=params["lam"], shape=wl.shape, precision=precision, R_U=params["R_U"], **kw)
+
+
+def closure_sizes(M: int):
+    """(F, O, packed weight count) of the closure network for M species."""
+    lib = load_library()
+    F, O, nw = ct.c_int(), ct.c_int(), ct.c_int()
+    rc = lib.lbm_mix_closure_sizes(int(M), ct.byref(F), ct.byref(O), ct.byref(nw))
+    if rc != 0:
+        raise LbmError(rc, lib.lbm_mix_last_error(None).decode())
+    return F.value, O.value, nw.value
 
 
 def conserved_sums_noalloc(pops, M: int, shape, sums, stream=None):

@@ -10,6 +10,7 @@
 #include "../../include/lbm_mix.h"
 #include "lbm_device.cuh"
 #include "lbm_dispatch.h"
+#include "lbm_train.h"
 
 namespace {
 
@@ -44,7 +45,7 @@ void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   d.N = s.N; d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.M = s.M; d.slaved = s.slaved; d.weak = s.weak;
   d.omega_is_fixed = s.omega_is_fixed; d.omega1_is_fixed = s.omega1_is_fixed;
   d.omega_fixed = (Real)s.omega_fixed; d.omega1_fixed = (Real)s.omega1_fixed;
-  d.R_U = (Real)s.R_U; d.cond_bound = (Real)s.cond_bound;
+  d.R_U = (Real)s.R_U; d.cond_bound = (Real)s.cond_bound; d.closure_bound = (Real)s.closure_bound;
   for (int a = 0; a < lbm::MAXM; ++a) {
     d.mass[a] = (Real)s.mass[a]; d.inv_mass[a] = (Real)s.inv_mass[a]; d.R_a[a] = (Real)s.R_a[a];
     d.Cv_a[a] = (Real)s.Cv_a[a]; d.Cp_a[a] = (Real)s.Cp_a[a]; d.mu[a] = (Real)s.mu[a];
@@ -157,11 +158,23 @@ struct lbm_mix {
   size_t stage_bytes = 0;
   long long steps = 0;
   long long launches = 0;
+  long long param_version = 0;   // bumped whenever the reference state (and so the parameter block) changes
   bool initialized = false;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;   // 4 per recorded step
   size_t ev_used = 0;
   std::string err;
+  // learned closure: FP32 master weights, Adam moments, gradient, bf16 image,
+  // accept/fallback counters, mini-batch scratch
+  int closure = 0;
+  float *d_w = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr;
+  unsigned char* d_img = nullptr;
+  unsigned long long* d_stats = nullptr;
+  double* d_loss = nullptr;
+  int adam_t = 0;
+  lbm::MlpScratch z{};
+  float* z_base = nullptr;
+  long long z_rows = 0;
 
   size_t need_pops() const { return (size_t)(M + 2) * 27 * (size_t)N * store_elem_bytes(prec); }
   size_t need_scratch() const { return (size_t)lbm::NSIDE * (size_t)N * side_elem_bytes(prec); }
@@ -169,6 +182,7 @@ struct lbm_mix {
     lbm::LaunchCtx c;
     c.N = N; c.stream = stream; c.pops = pops; c.side = scratch; c.err = d_err;
     c.partials = d_partials; c.p64 = &p64; c.p32 = &p32; c.base = d_base; c.ev = nullptr;
+    c.closure = closure; c.mlp_img = d_img; c.mlp_stats = d_stats;
     return c;
   }
   lbm_status fail(lbm_status s, const std::string& m) { err = m; return s; }
@@ -191,8 +205,26 @@ struct lbm_mix {
     if (s != LBM_OK) return s;
     s = cuda(cudaStreamSynchronize(stream), "stream synchronize");
     if (s != LBM_OK) return s;
+    if (flag & 4u) return fail(LBM_ERR_TIMEOUT, "a tensor-core completion wait timed out");
     if (flag) return fail(LBM_ERR_NONFINITE, "a node reached non-positive density or temperature (or NaN)");
     return LBM_OK;
+  }
+  lbm::MlpShape mlp_shape() const { return lbm::MlpShape{128, ks->mlp_F, ks->mlp_O, 3 * M}; }
+  // Mini-batch scratch for `rows` samples (grown on demand).
+  lbm_status ensure_train_scratch(long long rows) {
+    if (rows <= z_rows) return LBM_OK;
+    if (z_base) { cudaStreamSynchronize(stream); cudaFree(z_base); z_base = nullptr; z_rows = 0; }
+    const long long H = 128, O = ks->mlp_O;
+    lbm_status st = cuda(cudaMalloc(&z_base, sizeof(float) * (size_t)rows * (6 * H + 2 * O)), "cudaMalloc(training)");
+    if (st != LBM_OK) return st;
+    float* q = z_base;
+    z.h1 = q; q += rows * H; z.a1 = q; q += rows * H; z.h2 = q; q += rows * H; z.a2 = q; q += rows * H;
+    z.d1 = q; q += rows * H; z.d2 = q; q += rows * H; z.out = q; q += rows * O; z.dout = q;
+    z_rows = rows;
+    return LBM_OK;
+  }
+  lbm_status repack() {
+    return cuda(ks->mlp_pack(ctx(), d_w, d_img), "pack network image");
   }
   // Reference rest state (mass fractions Y, temperature T, density rho):
   // base tables of every lattice, their sums RL and the derived constants.
@@ -253,6 +285,7 @@ struct lbm_mix {
     if (st != LBM_OK) return st;
     st = cuda(cudaStreamSynchronize(stream), "synchronize");
     if (st == LBM_OK) has_reference = true;
+    ++param_version;
     return st;
   }
   // Host sums of nv reduced values (partials from the kernels above).
@@ -311,6 +344,117 @@ struct lbm_mix {
   }
 };
 
+// An ensemble of independent domains stepped together (one launch per kernel
+// for all of them).  Each domain is a full handle (its own constants,
+// reference state and buffers, carved from two shared allocations); the
+// batch keeps device tables of their parameter blocks, geometry, buffer
+// pointers and tiles, the launch shapes chosen by the autotuner, and a CUDA
+// graph of two consecutive steps (both AA parities).
+struct lbm_mix_batch {
+  int nd = 0, M = 0, prec = 0;
+  cudaStream_t user = nullptr;      // caller's stream
+  cudaStream_t stream = nullptr;    // internal stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<lbm_mix*> dom;
+  const lbm::KernelSet* ks = nullptr;
+  void* pops_all = nullptr;
+  void* side_all = nullptr;
+  size_t pops_total = 0, side_total = 0;
+  void* d_params = nullptr;
+  size_t param_bytes = 0;            // one parameter block
+  lbm::BatchGeom* d_geom = nullptr;
+  void** d_ptrs = nullptr;           // [nd] pops, then [nd] side
+  int2* d_tiles = nullptr;           // collide tiles, then stencil tiles for 128 and 256 threads
+  int ntiles_c = 0, ntiles_128 = 0, ntiles_256 = 0;
+  int grid_c = 0, grid_l = 0, block_l = 256;
+  int sm_count = 0;
+  unsigned* d_err = nullptr;
+  std::vector<long long> uploaded;   // parameter versions on the device
+  cudaGraphExec_t graph = nullptr;
+  bool use_graph = true;
+  long long steps = 0, nodes = 0;
+  std::string err;
+
+  lbm_status fail(lbm_status st, const std::string& m) { err = m; return st; }
+  lbm_status cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LBM_OK;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+  }
+  const int2* tiles_l() const { return d_tiles + ntiles_c + (block_l == 128 ? 0 : ntiles_128); }
+  int ntiles_l() const { return block_l == 128 ? ntiles_128 : ntiles_256; }
+  lbm::BatchCtx ctx() const {
+    lbm::BatchCtx c;
+    c.stream = stream; c.params = d_params; c.geom = d_geom;
+    c.pops = d_ptrs; c.side = d_ptrs + nd;
+    c.tiles_c = d_tiles; c.ntiles_c = ntiles_c; c.grid_c = grid_c;
+    c.tiles_l = tiles_l(); c.ntiles_l = ntiles_l(); c.grid_l = grid_l; c.block_l = block_l;
+    c.err = d_err;
+    return c;
+  }
+  void drop_graph() {
+    if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
+  }
+  // Parameter blocks of domains whose reference state changed since the last upload.
+  lbm_status upload_params() {
+    for (int d = 0; d < nd; ++d) {
+      if (uploaded[d] == dom[d]->param_version) continue;
+      const void* src = prec == LBM_PREC_FP64 ? (const void*)&dom[d]->p64 : (const void*)&dom[d]->p32;
+      lbm_status st = cuda(cudaMemcpyAsync((char*)d_params + (size_t)d * param_bytes, src, param_bytes,
+                                           cudaMemcpyHostToDevice, stream), "upload parameter block");
+      if (st != LBM_OK) return st;
+      uploaded[d] = dom[d]->param_version;
+    }
+    return cuda(cudaStreamSynchronize(stream), "synchronize");   // the host blocks must stay valid
+  }
+  lbm_status build_graph() {
+    drop_graph();
+    cudaGraph_t g = nullptr;
+    lbm_status st = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st != LBM_OK) return st;
+    const lbm::BatchCtx c = ctx();
+    cudaError_t e0 = ks->batch_step(c, 0);
+    cudaError_t e1 = ks->batch_step(c, 1);
+    cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    if (e0 != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda(e0 != cudaSuccess ? e0 : (e1 != cudaSuccess ? e1 : e2), "capture step graph");
+    }
+    st = cuda(cudaGraphInstantiate(&graph, g, 0), "instantiate step graph");
+    cudaGraphDestroy(g);
+    return st;
+  }
+  // nsteps steps of every domain on the internal stream (graph replays of two
+  // steps where the parity allows, single launches otherwise).
+  lbm_status run(int nsteps, bool graphs) {
+    int done = 0;
+    while (done < nsteps) {
+      const int parity = (int)((steps + done) & 1);
+      if (graphs && parity == 0 && nsteps - done >= 2) {
+        if (!graph) {
+          lbm_status st = build_graph();
+          if (st != LBM_OK) return st;
+        }
+        lbm_status st = cuda(cudaGraphLaunch(graph, stream), "graph launch");
+        if (st != LBM_OK) return st;
+        done += 2;
+      } else {
+        lbm_status st = cuda(ks->batch_step(ctx(), parity), "batched step kernels");
+        if (st != LBM_OK) return st;
+        done += 1;
+      }
+    }
+    return LBM_OK;
+  }
+  void advance(int nsteps) {
+    steps += nsteps;
+    for (lbm_mix* h : dom) {
+      h->steps += nsteps;
+      h->launches += (long long)nsteps * ks->launches_per_step;
+    }
+  }
+};
+
 extern "C" {
 
 int lbm_mix_num_outputs(int M) { return 6 + 5 * M; }
@@ -330,7 +474,7 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     if (p->bc[s] != LBM_BC_PERIODIC) { g_create_error = "only periodic boundaries are built"; return LBM_ERR_UNSUPPORTED; }
   if (p->precision < LBM_PREC_FP64 || p->precision > LBM_PREC_BF16_STORE) return bad("unknown precision");
   if (p->coupling != LBM_COUPLE_STRONG && p->coupling != LBM_COUPLE_WEAK) return bad("unknown coupling");
-  if (p->closure != LBM_CLOSURE_EXACT) { g_create_error = "only the exact Stefan-Maxwell closure is built"; return LBM_ERR_UNSUPPORTED; }
+  if (p->closure != LBM_CLOSURE_EXACT && p->closure != LBM_CLOSURE_MLP) return bad("unknown closure");
   const int slaved = p->slaved_species < 0 ? M - 1 : p->slaved_species;
   if (slaved >= M) return bad("slaved_species out of range");
   for (int a = 0; a < M; ++a) {
@@ -362,6 +506,10 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
 
   const lbm::KernelSet* ks = select_kernels(M, p->precision);
   if (!ks) { g_create_error = "no kernels built for this (M, precision)"; return LBM_ERR_UNSUPPORTED; }
+  if (p->closure == LBM_CLOSURE_MLP && !ks->mlp_step_ok) {
+    g_create_error = "the learned closure runs only in the FP32-arithmetic precisions with M >= 2";
+    return LBM_ERR_UNSUPPORTED;
+  }
 
   lbm_mix* h = new (std::nothrow) lbm_mix();
   if (!h) return bad("out of host memory");
@@ -376,6 +524,8 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   d.omega_is_fixed = p->omega_fixed > 0.0; d.omega1_is_fixed = p->omega1_fixed > 0.0;
   d.omega_fixed = p->omega_fixed; d.omega1_fixed = p->omega1_fixed; d.R_U = p->R_U;
   d.cond_bound = p->fp64_cond_bound > 0.0 ? p->fp64_cond_bound : 1e3;
+  d.closure_bound = p->closure_residual_bound > 0.0 ? p->closure_residual_bound : 1e-2;
+  h->closure = p->closure == LBM_CLOSURE_MLP;
   for (int a = 0; a < lbm::MAXM; ++a) {
     const bool on = a < M;
     const double ma = on ? p->molar_mass[a] : 1.0;
@@ -408,12 +558,29 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   if (e == cudaSuccess) e = cudaMalloc(&h->d_base, sizeof(double) * (lbm::MAXM + 2) * 27);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sums, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 256, h->stream);
+  // the closure network: zero weights (every node falls back until trained)
+  const size_t nw = (size_t)ks->mlp_nw;
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_w, 4 * nw * sizeof(float));
+  if (e == cudaSuccess) {
+    h->d_m = h->d_w + nw; h->d_v = h->d_m + nw; h->d_g = h->d_v + nw;
+    e = cudaMemsetAsync(h->d_w, 0, 4 * nw * sizeof(float), h->stream);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_img, (size_t)ks->mlp_img_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 2 * sizeof(unsigned long long) + sizeof(double));
+  if (e == cudaSuccess) {
+    h->d_loss = reinterpret_cast<double*>(h->d_stats + 2);
+    e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream);
+  }
+  if (e == cudaSuccess) e = ks->mlp_pack(h->ctx(), h->d_w, h->d_img);
   if (e != cudaSuccess) {
     g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_sums) cudaFree(h->d_sums);
     if (h->d_base) cudaFree(h->d_base);
+    if (h->d_w) cudaFree(h->d_w);
+    if (h->d_img) cudaFree(h->d_img);
+    if (h->d_stats) cudaFree(h->d_stats);
     delete h;
     return LBM_ERR_CUDA;
   }
@@ -622,12 +789,375 @@ int lbm_mix_kernel_times(lbm_mix_t h, double* ms, long long* counts, int nk) {
 long long lbm_mix_step_count(lbm_mix_t h) { return h ? h->steps : -1; }
 long long lbm_mix_launch_count(lbm_mix_t h) { return h ? h->launches : -1; }
 
+lbm_status lbm_mix_closure_sizes(int M, int* F, int* O, int* n_weights) {
+  const lbm::KernelSet* ks = select_kernels(M, LBM_PREC_FP32);
+  if (!ks) { g_create_error = "no kernels built for this species count"; return LBM_ERR_UNSUPPORTED; }
+  if (F) *F = ks->mlp_F;
+  if (O) *O = ks->mlp_O;
+  if (n_weights) *n_weights = ks->mlp_nw;
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_closure_set_weights(lbm_mix_t h, const float* w, int host_ptr) {
+  if (!h) return LBM_ERR_ARG;
+  if (!w) return h->fail(LBM_ERR_ARG, "NULL weights");
+  const size_t nw = (size_t)h->ks->mlp_nw;
+  lbm_status s = h->cuda(cudaMemcpyAsync(h->d_w, w, nw * sizeof(float),
+                                         host_ptr ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
+                         "copy weights");
+  if (s != LBM_OK) return s;
+  if ((s = h->cuda(cudaMemsetAsync(h->d_m, 0, 2 * nw * sizeof(float), h->stream), "reset Adam state")) != LBM_OK)
+    return s;
+  h->adam_t = 0;
+  if ((s = h->repack()) != LBM_OK) return s;
+  h->launches += 1;
+  if (host_ptr) return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_closure_get_weights(lbm_mix_t h, float* w, int host_ptr) {
+  if (!h) return LBM_ERR_ARG;
+  if (!w) return h->fail(LBM_ERR_ARG, "NULL output");
+  lbm_status s = h->cuda(cudaMemcpyAsync(w, h->d_w, (size_t)h->ks->mlp_nw * sizeof(float),
+                                         host_ptr ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
+                         "copy weights");
+  if (s != LBM_OK || !host_ptr) return s;
+  return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
+}
+
+lbm_status lbm_mix_closure_samples(lbm_mix_t h, float* features, float* targets) {
+  if (!h) return LBM_ERR_ARG;
+  if (!features || !targets) return h->fail(LBM_ERR_ARG, "NULL output");
+  if (!h->initialized) return h->fail(LBM_ERR_STATE, "no state");
+  lbm_status s = h->cuda(h->ks->samples(h->ctx(), (int)(h->steps & 1), features, targets), "samples kernel");
+  if (s == LBM_OK) h->launches += 1;
+  return s;
+}
+
+lbm_status lbm_mix_closure_forward(lbm_mix_t h, const float* features, float* outputs, long long n) {
+  if (!h) return LBM_ERR_ARG;
+  if (n < 0 || (n > 0 && (!features || !outputs))) return h->fail(LBM_ERR_ARG, "bad arguments");
+  if (n == 0) return LBM_OK;
+  lbm_status s = h->cuda(h->ks->mlp_forward(h->ctx(), features, outputs, n), "network kernel");
+  if (s == LBM_OK) h->launches += 1;
+  return s;
+}
+
+lbm_status lbm_mix_closure_loss_grad(lbm_mix_t h, const float* features, const float* targets, long long n,
+                                     float* grad, double* loss) {
+  if (!h) return LBM_ERR_ARG;
+  if (n <= 0 || n > (1LL << 30) || !features || !targets) return h->fail(LBM_ERR_ARG, "bad arguments");
+  lbm_status s = h->ensure_train_scratch(n);
+  if (s != LBM_OK) return s;
+  s = h->cuda(lbm::mlp_train_grad(h->stream, h->mlp_shape(), h->d_w, features, targets, (int)n, h->z,
+                                  grad ? grad : h->d_g, h->d_loss), "training kernels");
+  if (s != LBM_OK) return s;
+  h->launches += 16;
+  if (loss) {
+    if ((s = h->cuda(cudaMemcpyAsync(loss, h->d_loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                     "copy loss")) != LBM_OK)
+      return s;
+    return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_closure_train(lbm_mix_t h, const float* features, const float* targets, long long n, int batch,
+                                 int steps, double lr, double* last_loss) {
+  if (!h) return LBM_ERR_ARG;
+  if (n <= 0 || batch <= 0 || steps < 0 || !(lr > 0.0) || !features || !targets)
+    return h->fail(LBM_ERR_ARG, "bad arguments");
+  const long long rows_max = batch < n ? batch : n;
+  lbm_status s = h->ensure_train_scratch(rows_max);
+  if (s != LBM_OK) return s;
+  const int F = h->ks->mlp_F, O = h->ks->mlp_O;
+  const long long nw = h->ks->mlp_nw;
+  long long start = 0;
+  for (int it = 0; it < steps; ++it) {
+    const long long rows = (n - start) < rows_max ? (n - start) : rows_max;
+    s = h->cuda(lbm::mlp_train_grad(h->stream, h->mlp_shape(), h->d_w, features + start * F, targets + start * O,
+                                    (int)rows, h->z, h->d_g, h->d_loss), "training kernels");
+    if (s != LBM_OK) return s;
+    s = h->cuda(lbm::mlp_adam(h->stream, h->d_w, h->d_g, h->d_m, h->d_v, nw, (float)lr, ++h->adam_t), "Adam kernel");
+    if (s != LBM_OK) return s;
+    h->launches += 17;
+    start += rows;
+    if (start >= n) start = 0;
+  }
+  if ((s = h->repack()) != LBM_OK) return s;
+  h->launches += 1;
+  if (last_loss) {
+    *last_loss = 0.0;
+    if (steps > 0 &&
+        (s = h->cuda(cudaMemcpyAsync(last_loss, h->d_loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                     "copy loss")) != LBM_OK)
+      return s;
+  }
+  return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
+}
+
+lbm_status lbm_mix_closure_stats(lbm_mix_t h, long long* accepted, long long* fallback, int reset) {
+  if (!h) return LBM_ERR_ARG;
+  unsigned long long c[2] = {0, 0};
+  lbm_status s = h->cuda(cudaMemcpyAsync(c, h->d_stats, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "copy counters");
+  if (s != LBM_OK) return s;
+  if (reset && (s = h->cuda(cudaMemsetAsync(h->d_stats, 0, sizeof(c), h->stream), "reset counters")) != LBM_OK)
+    return s;
+  if ((s = h->cuda(cudaStreamSynchronize(h->stream), "synchronize")) != LBM_OK) return s;
+  if (accepted) *accepted = (long long)c[0];
+  if (fallback) *fallback = (long long)c[1];
+  return LBM_OK;
+}
+
+
+lbm_status lbm_mix_batch_create(const lbm_mix_params* params, int ndomains, void* cuda_stream,
+                                lbm_mix_batch_t* out) {
+  auto bad = [&](lbm_status st, const std::string& m) { g_create_error = m; return st; };
+  if (!out) return bad(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!params || ndomains < 1) return bad(LBM_ERR_ARG, "need at least one domain");
+  for (int d = 1; d < ndomains; ++d)
+    if (params[d].M != params[0].M || params[d].precision != params[0].precision ||
+        params[d].coupling != params[0].coupling)
+      return bad(LBM_ERR_ARG, "all domains must share M, precision and coupling");
+  for (int d = 0; d < ndomains; ++d)
+    if (params[d].closure != LBM_CLOSURE_EXACT) return bad(LBM_ERR_UNSUPPORTED, "batched domains use the exact closure");
+  lbm_mix_batch* b = new (std::nothrow) lbm_mix_batch();
+  if (!b) return bad(LBM_ERR_ARG, "out of host memory");
+  b->nd = ndomains; b->M = params[0].M; b->prec = params[0].precision;
+  b->user = (cudaStream_t)cuda_stream;
+  auto cleanup = [&](lbm_status st) {
+    lbm_mix_batch_destroy(b);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(bad(LBM_ERR_CUDA, "stream/event creation failed"));
+  for (int d = 0; d < ndomains; ++d) {
+    lbm_mix_t h = nullptr;
+    lbm_status st = lbm_mix_create(&params[d], cuda_stream, &h);
+    if (st != LBM_OK) {
+      g_create_error = "domain " + std::to_string(d) + ": " + g_create_error;
+      return cleanup(st);
+    }
+    b->dom.push_back(h);
+  }
+  b->ks = b->dom[0]->ks;
+  // one allocation each for populations and scratch, 256-byte aligned slices
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  std::vector<size_t> po(ndomains), so(ndomains);
+  for (int d = 0; d < ndomains; ++d) {
+    po[d] = b->pops_total; b->pops_total += up(b->dom[d]->need_pops());
+    so[d] = b->side_total; b->side_total += up(b->dom[d]->need_scratch());
+    b->nodes += b->dom[d]->N;
+  }
+  if (cudaMalloc(&b->pops_all, b->pops_total) != cudaSuccess || cudaMalloc(&b->side_all, b->side_total) != cudaSuccess)
+    return cleanup(bad(LBM_ERR_CUDA, "cudaMalloc of the ensemble buffers failed"));
+  std::vector<void*> ptrs(2 * ndomains);
+  std::vector<lbm::BatchGeom> geom(ndomains);
+  for (int d = 0; d < ndomains; ++d) {
+    lbm_mix* h = b->dom[d];
+    ptrs[d] = (char*)b->pops_all + po[d];
+    ptrs[ndomains + d] = (char*)b->side_all + so[d];
+    if (lbm_mix_bind_buffers(h, ptrs[d], h->need_pops(), ptrs[ndomains + d], h->need_scratch()) != LBM_OK)
+      return cleanup(bad(LBM_ERR_ARG, "binding domain buffers failed"));
+    geom[d] = lbm::BatchGeom{h->N, h->p64.nx, h->p64.ny, h->p64.nz};
+  }
+  // tiles: (domain, first node) for the collide block and for 128/256-thread stencil blocks
+  std::vector<int2> tiles;
+  auto add_tiles = [&](int bs) {
+    int cnt = 0;
+    for (int d = 0; d < ndomains; ++d)
+      for (long long n0 = 0; n0 < b->dom[d]->N; n0 += bs) { tiles.push_back(make_int2(d, (int)n0)); ++cnt; }
+    return cnt;
+  };
+  b->ntiles_c = add_tiles(b->ks->collide_bs);
+  b->ntiles_128 = add_tiles(128);
+  b->ntiles_256 = add_tiles(256);
+  b->param_bytes = b->prec == LBM_PREC_FP64 ? sizeof(lbm::DevParams<double>) : sizeof(lbm::DevParams<float>);
+  cudaError_t e = cudaMalloc(&b->d_params, b->param_bytes * ndomains);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_geom, sizeof(lbm::BatchGeom) * ndomains);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void*) * 2 * ndomains);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(int2) * tiles.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, 256);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_geom, geom.data(), sizeof(lbm::BatchGeom) * ndomains, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ptrs, ptrs.data(), sizeof(void*) * 2 * ndomains, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 256);
+  if (e == cudaSuccess) e = b->ks->batch_prepare();
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cleanup(bad(LBM_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e)));
+  b->uploaded.assign(ndomains, -1);
+  // default launch shapes (the autotuner may replace them): one block per tile
+  b->grid_c = b->ntiles_c;
+  b->block_l = 256;
+  b->grid_l = b->ntiles_256;
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_domain(lbm_mix_batch_t b, int d, lbm_mix_t* h) {
+  if (!b || !h) return LBM_ERR_ARG;
+  if (d < 0 || d >= b->nd) return b->fail(LBM_ERR_ARG, "domain index out of range");
+  *h = b->dom[d];
+  return LBM_OK;
+}
+
+long long lbm_mix_batch_nodes(lbm_mix_batch_t b) { return b ? b->nodes : -1; }
+
+lbm_status lbm_mix_batch_step(lbm_mix_batch_t b, int nsteps) {
+  if (!b) return LBM_ERR_ARG;
+  if (nsteps < 0) return b->fail(LBM_ERR_ARG, "nsteps < 0");
+  for (lbm_mix* h : b->dom) {
+    if (!h->initialized) return b->fail(LBM_ERR_STATE, "every domain needs init_fields or set_populations first");
+    if (h->steps != b->steps) return b->fail(LBM_ERR_STATE, "a domain was stepped on its own; its parity differs");
+  }
+  lbm_status st;
+  if ((st = b->cuda(cudaEventRecord(b->ev_in, b->user), "record")) != LBM_OK) return st;
+  if ((st = b->cuda(cudaStreamWaitEvent(b->stream, b->ev_in, 0), "wait")) != LBM_OK) return st;
+  if ((st = b->upload_params()) != LBM_OK) return st;
+  if ((st = b->run(nsteps, b->use_graph)) != LBM_OK) return st;
+  if ((st = b->cuda(cudaEventRecord(b->ev_out, b->stream), "record")) != LBM_OK) return st;
+  if ((st = b->cuda(cudaStreamWaitEvent(b->user, b->ev_out, 0), "wait")) != LBM_OK) return st;
+  b->advance(nsteps);
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* config, double* best_ms) {
+  if (!b) return LBM_ERR_ARG;
+  if (trial_steps < 1) return b->fail(LBM_ERR_ARG, "trial_steps < 1");
+  for (lbm_mix* h : b->dom)
+    if (!h->initialized || h->steps != b->steps) return b->fail(LBM_ERR_STATE, "initialise every domain first");
+  lbm_status st;
+  if ((st = b->cuda(cudaStreamSynchronize(b->user), "synchronize")) != LBM_OK) return st;
+  if ((st = b->upload_params()) != LBM_OK) return st;
+  // save the state: the trials step it
+  void *sp = nullptr, *ss = nullptr;
+  if ((st = b->cuda(cudaMalloc(&sp, b->pops_total), "cudaMalloc(autotune)")) != LBM_OK) return st;
+  if ((st = b->cuda(cudaMalloc(&ss, b->side_total), "cudaMalloc(autotune)")) != LBM_OK) { cudaFree(sp); return st; }
+  cudaMemcpyAsync(sp, b->pops_all, b->pops_total, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(ss, b->side_all, b->side_total, cudaMemcpyDeviceToDevice, b->stream);
+  const long long steps0 = b->steps;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto trial = [&](double& ms) -> lbm_status {
+    lbm_status s2 = b->run(1, false);                        // warm-up
+    if (s2 != LBM_OK) return s2;
+    b->steps += 1;
+    cudaEventRecord(e0, b->stream);
+    if ((s2 = b->run(trial_steps, false)) != LBM_OK) return s2;
+    cudaEventRecord(e1, b->stream);
+    b->steps += trial_steps;
+    if ((s2 = b->cuda(cudaEventSynchronize(e1), "synchronize")) != LBM_OK) return s2;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms = (double)t / trial_steps;
+    return LBM_OK;
+  };
+  const int sm = b->sm_count > 0 ? b->sm_count : 1;
+  std::vector<int> gc = {b->ntiles_c, sm, 2 * sm, 3 * sm, 4 * sm};
+  double best = 1e300;
+  int bc = b->ntiles_c, bl = 256, bg = b->ntiles_256;
+  st = LBM_OK;
+  b->block_l = 256; b->grid_l = b->ntiles_256;
+  for (int g : gc) {
+    if (g > b->ntiles_c || st != LBM_OK) continue;
+    b->grid_c = g;
+    double ms;
+    if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bc = g; }
+  }
+  b->grid_c = bc;
+  for (int blk : {128, 256}) {
+    const int nt = blk == 128 ? b->ntiles_128 : b->ntiles_256;
+    for (int g : {nt, 8 * sm, 16 * sm}) {
+      if (g > nt || st != LBM_OK) continue;
+      b->block_l = blk; b->grid_l = g;
+      double ms;
+      if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bl = blk; bg = g; }
+    }
+  }
+  b->block_l = bl; b->grid_l = bg;
+  b->drop_graph();
+  // restore the state and the step count
+  cudaMemcpyAsync(b->pops_all, sp, b->pops_total, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(b->side_all, ss, b->side_total, cudaMemcpyDeviceToDevice, b->stream);
+  lbm_status s3 = b->cuda(cudaStreamSynchronize(b->stream), "synchronize");
+  b->steps = steps0;
+  cudaFree(sp);
+  cudaFree(ss);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  if (s3 != LBM_OK) return s3;
+  if (config) { config[0] = b->grid_c; config[1] = b->block_l; config[2] = b->grid_l; }
+  if (best_ms) *best_ms = best;
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_set_config(lbm_mix_batch_t b, int grid_collide, int block_stencil, int grid_stencil,
+                                    int use_graph) {
+  if (!b) return LBM_ERR_ARG;
+  if (block_stencil != 128 && block_stencil != 256) return b->fail(LBM_ERR_ARG, "stencil blocks are 128 or 256 threads");
+  const int ntl = block_stencil == 128 ? b->ntiles_128 : b->ntiles_256;
+  if (grid_collide < 1 || grid_collide > b->ntiles_c || grid_stencil < 1 || grid_stencil > ntl)
+    return b->fail(LBM_ERR_ARG, "grid sizes must be in 1..number of tiles");
+  b->grid_c = grid_collide; b->block_l = block_stencil; b->grid_l = grid_stencil;
+  b->use_graph = use_graph != 0;
+  b->drop_graph();
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_config(lbm_mix_batch_t b, int* config) {
+  if (!b || !config) return LBM_ERR_ARG;
+  config[0] = b->grid_c; config[1] = b->block_l; config[2] = b->grid_l; config[3] = b->use_graph ? 1 : 0;
+  config[4] = b->ntiles_c; config[5] = b->ntiles_128; config[6] = b->ntiles_256; config[7] = b->ks->collide_bs;
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_synchronize(lbm_mix_batch_t b) {
+  if (!b) return LBM_ERR_ARG;
+  unsigned flag = 0;
+  lbm_status st = b->cuda(cudaStreamSynchronize(b->user), "synchronize");
+  if (st != LBM_OK) return st;
+  if ((st = b->cuda(cudaMemcpy(&flag, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error flag")) != LBM_OK)
+    return st;
+  if (flag) return b->fail(LBM_ERR_NONFINITE, "a node reached non-positive density or temperature (or NaN)");
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_batch_destroy(lbm_mix_batch_t b) {
+  if (!b) return LBM_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->drop_graph();
+  for (lbm_mix* h : b->dom) lbm_mix_destroy(h);
+  if (b->pops_all) cudaFree(b->pops_all);
+  if (b->side_all) cudaFree(b->side_all);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->d_geom) cudaFree(b->d_geom);
+  if (b->d_ptrs) cudaFree(b->d_ptrs);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_err) cudaFree(b->d_err);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LBM_OK;
+}
+
+const char* lbm_mix_batch_last_error(lbm_mix_batch_t b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
 lbm_status lbm_mix_destroy(lbm_mix_t h) {
   if (!h) return LBM_ERR_ARG;
   cudaStreamSynchronize(h->stream);
   if (h->owns_buffers) { cudaFree(h->pops); cudaFree(h->scratch); }
   if (h->d_stage) cudaFree(h->d_stage);
   cudaFree(h->d_err); cudaFree(h->d_partials); cudaFree(h->d_sums); cudaFree(h->d_base);
+  cudaFree(h->d_w); cudaFree(h->d_img); cudaFree(h->d_stats);
+  if (h->z_base) cudaFree(h->z_base);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return LBM_OK;

@@ -11,14 +11,17 @@
 #pragma once
 
 #include "lbm_stencil.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
 // Threads per block: the deviations of all S lattices are staged in shared
-// memory (S * 27 values per thread), kept near 110 KB per block.
-template <int M, class Real>
+// memory (S * 27 values per thread), kept near 110 KB per block.  With the
+// learned closure (CL = 1) a block is one 128-node tile of the network.
+template <int M, class Real, int CL = 0>
 constexpr int collide_block() {
   constexpr long long per = (long long)(M + 2) * 27 * sizeof(Real);
+  if constexpr (CL) return MLP_TILE;
   return per * 128 <= 113 * 1024 ? 128 : (per * 64 <= 113 * 1024 ? 64 : 32);
 }
 
@@ -29,30 +32,49 @@ constexpr int collide_block() {
 #ifndef LBM_COLLIDE_MINB
 #define LBM_COLLIDE_MINB 3
 #endif
-template <int M, class Real>
+template <int M, class Real, int CL = 0>
 constexpr int collide_min_blocks() {
+  if constexpr (CL) return 1;
   constexpr long long bytes = (long long)(M + 2) * 27 * sizeof(Real) * collide_block<M, Real>();
   constexpr long long nb = (227LL * 1024) / bytes;
   constexpr int fit = nb >= 4 ? 4 : (nb < 1 ? 1 : (int)nb);
   return LBM_COLLIDE_MINB < fit ? LBM_COLLIDE_MINB : fit;
 }
 
-template <int M, class Real>
-constexpr size_t collide_smem() {
-  return (size_t)(M + 2) * Q * collide_block<M, Real>() * sizeof(Real);
+template <int M, class Real, int CL = 0>
+constexpr size_t collide_stage_bytes() {
+  return (size_t)(M + 2) * Q * collide_block<M, Real, CL>() * sizeof(Real);
 }
+template <int M, class Real, int CL = 0>
+constexpr size_t collide_smem() {
+  if constexpr (CL) return collide_stage_bytes<M, Real, CL>() + MlpDims<M>::SMEM;
+  return collide_stage_bytes<M, Real, CL>();
+}
+// The network closure exists for the FP32-arithmetic paths with M >= 2.
+template <int M, class Real>
+constexpr bool kMlpOk = (M >= 2) && sizeof(Real) == 4;
 
-template <int M, class Real, class Store, int PAR>
-__global__ void __launch_bounds__(collide_block<M, Real>(), collide_min_blocks<M, Real>())
-collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
-               unsigned* __restrict__ err) {
-  constexpr int BS = collide_block<M, Real>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One node's collide + stream (thread threadIdx.x of the block; the block's
+// shared memory holds the stage and, with CL = 1, the network's tile).
+template <int M, class Real, class Store, int PAR, int CL>
+__device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __restrict__ pops,
+                                             Real* __restrict__ side, unsigned* __restrict__ err,
+                                             const unsigned char* __restrict__ mlp_img,
+                                             unsigned long long* __restrict__ mlp_stats, long long n_raw,
+                                             unsigned char* smem_raw) {
+  constexpr int BS = collide_block<M, Real, CL>();
   Real* sm = reinterpret_cast<Real*>(smem_raw);     // [(M+2)*27][BS], thread-private columns
-  const long long n = gtid();
-  if (n >= p.N) return;
   const long long N = p.N;
   const int tid = threadIdx.x;
+  // With the network every thread of the block takes part in its tile; the
+  // threads past the grid compute on a copy of the last node and store nothing.
+  const bool active = n_raw < N;
+  if constexpr (!CL) {
+    if (!active) return;
+  }
+  const long long n = active ? n_raw : N - 1;
+  MlpBlock<M> mlp{smem_raw + collide_stage_bytes<M, Real, CL>(), 0u, 0u};
+  if constexpr (CL) mlp.begin_setup(mlp_img);
   const Nbr nb = make_nbr(p, n);
 
   // a1 + a2: load (AA addressing), add the deferred terms of the previous
@@ -116,7 +138,7 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
       if (a == p.slaved) { ja[a][0] = j[0] - o[0]; ja[a][1] = j[1] - o[1]; ja[a][2] = j[2] - o[2]; }
   }
   const Real rho = th.rho;
-  if (!(rho > Real(0)) || !(th.T > Real(0)) || !(th.rho_sp > Real(0))) atomicOr(err, 1u);
+  if (active && (!(rho > Real(0)) || !(th.T > Real(0)) || !(th.rho_sp > Real(0)))) atomicOr(err, 1u);
   const Real om = th.omega;
   const Real om1 = omega1_of<M, Real>(p, th);
   const Real P = th.P, T = th.T;
@@ -124,7 +146,7 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
   // a5: this node's side fields: Phi_alpha = j_alpha (1 - 3RT) - rho u_alpha^3 and
   // c_omega = 1/omega - 1/2 (Eq. Xalpha); C_p and s = (1/2)(2 - omega_1) P T / theta
   // (sum_a H_a grad Y_a = T grad C_p for constant specific heats, Eq. corrFourier).
-  {
+  if (active) {
     const Real a3 = Real(1) - Real(3) * th.theta;
 #pragma unroll
     for (int c = 0; c < 3; ++c) side[(SP_PHI + c) * N + n] = j[c] * a3 - rho * th.u[c] * th.u[c] * th.u[c];
@@ -142,7 +164,57 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
 #pragma unroll
     for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
   Real J[M][3];
-  sm_solve<M, Real>(p, th, itab, ja, J);
+  if constexpr (CL) {
+    // a6': the network proposes the normalised fluxes; it is accepted where
+    // the residual of the J-form system stays within the bound, else the
+    // exact solve runs (Eq. transform12).
+    Real r[M][3], sr = Real(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r[a][c] = ja[a][c] - th.rho_a[a] * th.u_sp[c];
+        sr = fmax(sr, fabs(r[a][c]));
+      }
+    const Real inv_s = sr > Real(0) ? Real(1) / sr : Real(0);
+    {
+      float f[MlpDims<M>::F];
+      sm_feature_values<M, Real>(p, th, itab, r, inv_s, f);
+#pragma unroll
+      for (int k0 = 0; k0 < MlpDims<M>::F; k0 += 8) store_row8(mlp.act(), tid, k0, MlpDims<M>::F, f + k0);
+    }
+    mlp.finish_setup();
+    float out[MlpDims<M>::O];
+    const bool ran = mlp.forward(out, err);
+    // J~ = J0 + correction, J0 = (r / s) / A_aa the one-sweep Jacobi estimate
+    Real rn[M][3], Jn[M][3], diag[M];
+    sm_diagonal<M, Real>(th, itab, diag);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rn[a][c] = r[a][c] * inv_s;
+        Jn[a][c] = rn[a][c] / diag[a] + (Real)out[3 * a + c];
+      }
+    const Real res = sm_residual<M, Real>(th, itab, diag, rn, Jn);
+    const bool accept = ran && (sr == Real(0) || res <= p.closure_bound);
+    if (accept) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) J[a][c] = sr * Jn[a][c];
+    } else {
+      sm_solve<M, Real>(p, th, itab, ja, J);
+    }
+    const unsigned acc = __ballot_sync(0xffffffffu, active && accept);
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if ((tid & 31) == 0 && act) {
+      atomicAdd(&mlp_stats[0], (unsigned long long)__popc(acc));
+      atomicAdd(&mlp_stats[1], (unsigned long long)__popc(act & ~acc));
+    }
+  } else {
+    sm_solve<M, Real>(p, th, itab, ja, J);
+  }
   Real V[M][3], beta[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -177,13 +249,13 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
         const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
         s_f += e;
         const Real fv = sm[(M * Q + i) * BS + tid];
-        codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * (e - fv));
+        if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * (e - fv));
       }
     });
     long long node; int slot;
     aa_write_loc(PAR, nbw, n, 13, node, slot);
     const Real fv = sm[(M * Q + 13) * BS + tid];
-    codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
+    if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
   }
 
   // a9: energy lattice.  With N = R^eq - rho E theta I, Eqs. (geq2mom),
@@ -263,14 +335,16 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
         const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
         s_g += e;
         const Real gv = sm[((M + 1) * Q + i) * BS + tid];
-        codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
-                                 gv + om * (e - gv) + wi * dotc<Real, i>(mvec));
+        if (active)
+          codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
+                                   gv + om * (e - gv) + wi * dotc<Real, i>(mvec));
       }
     });
     long long node; int slot;
     aa_write_loc(PAR, nbw, n, 13, node, slot);
     const Real gv = sm[((M + 1) * Q + 13) * BS + tid];
-    codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
+    if (active)
+      codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
   }
 
   // a7: species, Eqs. (SMlbm), (fstar1).  Equilibrium deviation
@@ -288,11 +362,14 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
 #pragma unroll
       for (int c = 0; c < 3; ++c) ev[b][c] = V[b][c] * (Real(2) * th.u_sp[c] + V[b][c]);
     }
-    Real kap[M][M];
+    // F_ai = Y_a sum_b (1/tau_ab) rho_b Dif_bi with 1/tau_ab = R_U T m C_ab:
+    // the constants C_ab stay in the parameter block, no M x M array is live.
+    Real tY[M];
+    {
+      const Real tm = p.R_U * th.T * th.m;
 #pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-      for (int b = 0; b < M; ++b) kap[a][b] = th.Y[a] * th.rho_a[b] * itab[a][b];
+      for (int a = 0; a < M; ++a) tY[a] = tm * th.Y[a];
+    }
     Real s_e[M], s_F[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) { s_e[a] = Real(0); s_F[a] = Real(0); }
@@ -315,19 +392,21 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
           const Real ty = pf_v<Real>(cy, V[b][1], ev[b][1]);
           const Real tz = pf_v<Real>(cz, V[b][2], ev[b][2]);
           const Real sx = ax - tx, sy = ay - ty;
-          Dif[b] = tx * ay * az + sx * ty * az + sx * sy * tz;
+          Dif[b] = th.rho_a[b] * (tx * ay * az + sx * ty * az + sx * sy * tz);
         }
 #pragma unroll
         for (int a = 0; a < M; ++a) {
           Real F = Real(0);
 #pragma unroll
-          for (int b = 0; b < M; ++b) F += kap[a][b] * Dif[b];
+          for (int b = 0; b < M; ++b) F += p.Cab[a][b] * Dif[b];
+          F *= tY[a];
           const Real e = th.rho_a[a] * pf_diff<Real, i>(th.u_sp, x2, zr[a], dz[a])
                        + th.rho_a_dev[a] * pf_ref<Real, i>(zr[a]);
           s_e[a] += e; s_F[a] += F;
           const Real kv = sm[(a * Q + i) * BS + tid];
-          codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
-                                   kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
+          if (active)
+            codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
+                                     kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
         }
       }
     });
@@ -337,10 +416,21 @@ collide_kernel(const DevParams<Real> p, Store* __restrict__ pops, Real* __restri
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];
       const Real kv = sm[(a * Q + 13) * BS + tid];
-      codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
-                               kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
+      if (active)
+        codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
+                                 kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
     }
   }
+  if constexpr (CL) mlp.teardown();
+}
+
+template <int M, class Real, class Store, int PAR, int CL = 0>
+__global__ void __launch_bounds__(collide_block<M, Real, CL>(), collide_min_blocks<M, Real, CL>())
+collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
+               unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
+               unsigned long long* __restrict__ mlp_stats) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  collide_node<M, Real, Store, PAR, CL>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
 }
 
 }  // namespace lbm

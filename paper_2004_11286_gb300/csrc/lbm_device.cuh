@@ -57,6 +57,7 @@ struct DevParams {
   Real R_U;
   Real rho_eps;          // V_a = 0 where rho_a <= rho_eps * rho
   Real cond_bound;       // FP64 re-solve threshold for the SM system (FP32 paths)
+  Real closure_bound;    // learned closure: largest accepted residual of the J-form system
   Real mass[MAXM];
   Real inv_mass[MAXM];
   Real R_a[MAXM];
@@ -112,8 +113,9 @@ struct Nbr {
   }
 };
 
-template <class Real>
-__device__ __forceinline__ Nbr make_nbr(const DevParams<Real>& p, long long n_) {
+// Periodic neighbour table of node n on the grid of p (any type with nx, ny, nz).
+template <class P>
+__device__ __forceinline__ Nbr make_nbr(const P& p, long long n_) {
   Nbr b;
   const unsigned n = (unsigned)n_;
   const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;

@@ -19,6 +19,27 @@ struct LaunchCtx {
   const DevParams<float>* p32;
   const double* base;   // device table [S][27] of the reference rest equilibria
   cudaEvent_t* ev;   // 4 events bracketing the step's kernels, or nullptr
+  int closure;                          // 1: learned closure in the step
+  const unsigned char* mlp_img;         // device bf16/FP32 image of the network
+  unsigned long long* mlp_stats;        // [accepted, fallback] node counters
+};
+
+// Batched ensemble: many independent domains stepped by single launches.
+struct BatchGeom {
+  long long N;
+  int nx, ny, nz;
+};
+struct BatchCtx {
+  cudaStream_t stream;
+  const void* params;       // DevParams<Real>[domains] (device)
+  const BatchGeom* geom;    // [domains] (device)
+  void* const* pops;        // per-domain population buffers (device array of device pointers)
+  void* const* side;        // per-domain scratch buffers
+  const int2* tiles_c;      // collide tiles (domain, first node), collide_bs nodes each
+  int ntiles_c, grid_c;
+  const int2* tiles_l;      // stencil tiles, block_l nodes each
+  int ntiles_l, grid_l, block_l;
+  unsigned* err;
 };
 
 struct KernelSet {
@@ -28,7 +49,15 @@ struct KernelSet {
   cudaError_t (*get_pops)(const LaunchCtx&, int parity, double* out);
   cudaError_t (*set_pops)(const LaunchCtx&, int parity, const double* in);
   cudaError_t (*diag)(const LaunchCtx&, int parity, double* d_sums);
+  cudaError_t (*samples)(const LaunchCtx&, int parity, float* feat, float* tgt);
+  cudaError_t (*mlp_forward)(const LaunchCtx&, const float* feat, float* out, long long n);
+  cudaError_t (*mlp_pack)(const LaunchCtx&, const float* w, unsigned char* img);
+  cudaError_t (*batch_prepare)();
+  cudaError_t (*batch_step)(const BatchCtx&, int parity);
   int launches_per_step;
+  int collide_bs;                            // nodes per collide block
+  int mlp_F, mlp_O, mlp_nw, mlp_img_bytes;   // network sizes for this species count
+  int mlp_step_ok;                           // the step can run the learned closure
 };
 
 // One launcher table per (species count, precision); see inst_m*_*.cu.

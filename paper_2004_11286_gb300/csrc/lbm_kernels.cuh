@@ -15,6 +15,7 @@
 #pragma once
 
 #include "lbm_collide.cuh"
+#include "lbm_batch.cuh"
 #include "lbm_readers.cuh"
 
 namespace lbm {
@@ -177,26 +178,77 @@ struct Launch {
         *c.p64, (Store*)c.pops, c.base, X, u, T, Pr);
     return cudaGetLastError();
   }
-  static cudaError_t step(const LaunchCtx& c, int parity) {
-    Real* side = (Real*)c.side;
-    constexpr int BS = collide_block<M, Real>();
-    constexpr size_t smem = collide_smem<M, Real>();
+  template <int CL>
+  static void collide(const LaunchCtx& c, int parity, Real* side) {
+    constexpr int BS = collide_block<M, Real, CL>();
+    constexpr size_t smem = collide_smem<M, Real, CL>();
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr = true;
     }
-    if (c.ev) cudaEventRecord(c.ev[0], c.stream);
     if (parity == 0)
-      collide_kernel<M, Real, Store, 0><<<grid_for(c.N, BS), BS, smem, c.stream>>>(P(c), (Store*)c.pops, side, c.err);
+      collide_kernel<M, Real, Store, 0, CL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
     else
-      collide_kernel<M, Real, Store, 1><<<grid_for(c.N, BS), BS, smem, c.stream>>>(P(c), (Store*)c.pops, side, c.err);
+      collide_kernel<M, Real, Store, 1, CL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
+  }
+  static cudaError_t step(const LaunchCtx& c, int parity) {
+    Real* side = (Real*)c.side;
+    if (c.ev) cudaEventRecord(c.ev[0], c.stream);
+    if constexpr (kMlpOk<M, Real>) {
+      if (c.closure) collide<1>(c, parity, side);
+      else collide<0>(c, parity, side);
+    } else {
+      collide<0>(c, parity, side);
+    }
     if (c.ev) cudaEventRecord(c.ev[1], c.stream);
     grad_GK_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[2], c.stream);
     grad_X_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[3], c.stream);
+    return cudaGetLastError();
+  }
+  static cudaError_t batch_prepare() {
+    constexpr size_t smem = collide_smem<M, Real>();
+    cudaFuncSetAttribute(collide_batch_kernel<M, Real, Store, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(collide_batch_kernel<M, Real, Store, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaGetLastError();
+  }
+  static cudaError_t batch_step(const BatchCtx& b, int parity) {
+    constexpr int BS = collide_block<M, Real>();
+    constexpr size_t smem = collide_smem<M, Real>();
+    const DevParams<Real>* prm = static_cast<const DevParams<Real>*>(b.params);
+    if (parity == 0)
+      collide_batch_kernel<M, Real, Store, 0><<<b.grid_c, BS, smem, b.stream>>>(prm, b.pops, b.side, b.tiles_c,
+                                                                                 b.ntiles_c, b.err);
+    else
+      collide_batch_kernel<M, Real, Store, 1><<<b.grid_c, BS, smem, b.stream>>>(prm, b.pops, b.side, b.tiles_c,
+                                                                                 b.ntiles_c, b.err);
+    grad_GK_batch_kernel<Real><<<b.grid_l, b.block_l, 0, b.stream>>>(b.geom, b.side, b.tiles_l, b.ntiles_l);
+    grad_X_batch_kernel<Real><<<b.grid_l, b.block_l, 0, b.stream>>>(b.geom, b.side, b.tiles_l, b.ntiles_l);
+    return cudaGetLastError();
+  }
+  static cudaError_t samples(const LaunchCtx& c, int parity, float* feat, float* tgt) {
+    closure_samples_kernel<M, Real, Store><<<grid_for(c.N, BLOCK), BLOCK, 0, c.stream>>>(
+        P(c), (const Store*)c.pops, (const Real*)c.side, parity, feat, tgt);
+    return cudaGetLastError();
+  }
+  static cudaError_t mlp_forward(const LaunchCtx& c, const float* feat, float* out, long long n) {
+    constexpr int smem = MlpDims<M>::SMEM;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(mlp_forward_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    if (n > 0)
+      mlp_forward_kernel<M><<<grid_for(n, MLP_TILE), MLP_TILE, smem, c.stream>>>(c.mlp_img, feat, out, n, c.err);
+    return cudaGetLastError();
+  }
+  static cudaError_t mlp_pack(const LaunchCtx& c, const float* w, unsigned char* img) {
+    mlp_pack_kernel<M><<<grid_for(MlpDims<M>::NW, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(w, img);
     return cudaGetLastError();
   }
   static cudaError_t moments(const LaunchCtx& c, int parity, double* out) {
@@ -225,7 +277,13 @@ struct Launch {
     KernelSet k;
     k.init = &init; k.step = &step; k.moments = &moments; k.get_pops = &get_pops;
     k.set_pops = &set_pops; k.diag = &diag;
+    k.samples = &samples; k.mlp_forward = &mlp_forward; k.mlp_pack = &mlp_pack;
+    k.batch_prepare = &batch_prepare; k.batch_step = &batch_step;
     k.launches_per_step = 3;
+    k.collide_bs = collide_block<M, Real>();
+    k.mlp_F = MlpDims<M>::F; k.mlp_O = MlpDims<M>::O; k.mlp_nw = MlpDims<M>::NW;
+    k.mlp_img_bytes = MlpDims<M>::IMG_BYTES;
+    k.mlp_step_ok = kMlpOk<M, Real> ? 1 : 0;
     return k;
   }
 };

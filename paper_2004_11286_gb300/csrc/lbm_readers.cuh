@@ -5,6 +5,7 @@
 #pragma once
 
 #include "lbm_stencil.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
@@ -98,6 +99,79 @@ set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const double*
     for (int L = 0; L < M + 2; ++L)
       codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L, (Real)(in[(L * Q + i) * N + n] - base[L * Q + i]));
   }
+}
+
+// Training pairs of the learned closure at every node: the network's
+// features (lbm_mlp.cuh) and its exact target, the correction of the exact
+// normalised fluxes J_a / s of the J-form system of Eq. (transform12)
+// (solved in FP64) to their one-sweep Jacobi estimate.
+template <int M, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK)
+closure_samples_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const Real* __restrict__ side,
+                       int parity, float* __restrict__ feat, float* __restrict__ tgt) {
+  using Dm = MlpDims<M>;
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const Nbr nb = make_nbr(p, n);
+  Real rdev[M], ja[M][3], rho_dev, j[3], rhoE_dev;
+  load_state_moments<M, Real, Store>(p, pops, side, parity, nb, n, rdev, ja, rho_dev, j, rhoE_dev);
+  Real jsum[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int a = 0; a < M; ++a) { jsum[0] += ja[a][0]; jsum[1] += ja[a][1]; jsum[2] += ja[a][2]; }
+  Thermo<M, Real> th;
+  thermo_state<M, Real>(p, rdev, jsum, rho_dev, j, rhoE_dev, th);
+  if (!p.weak) {
+    Real o[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a != p.slaved) { o[0] += ja[a][0]; o[1] += ja[a][1]; o[2] += ja[a][2]; }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a == p.slaved) { ja[a][0] = j[0] - o[0]; ja[a][1] = j[1] - o[1]; ja[a][2] = j[2] - o[2]; }
+  }
+  Real itab[M][M], r[M][3], sr = Real(0);
+  const Real tm = p.R_U * th.T * th.m;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+#pragma unroll
+    for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r[a][c] = ja[a][c] - th.rho_a[a] * th.u_sp[c];
+      sr = fmax(sr, fabs(r[a][c]));
+    }
+  }
+  const Real inv_s = sr > Real(0) ? Real(1) / sr : Real(0);
+  float f[Dm::F];
+  sm_feature_values<M, Real>(p, th, itab, r, inv_s, f);
+#pragma unroll
+  for (int k = 0; k < Dm::F; ++k) feat[n * Dm::F + k] = f[k];
+  double A64[M][M], r64[M][3], J64[M][3];
+  const double T = (double)th.T, m = (double)th.m;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    double diag = 1.0;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      if (b != a) {
+        const double it = (double)p.R_U * T * m * p.Cab64[a][b];
+        diag += 0.5 * it * (double)th.Y[b];
+        A64[a][b] = -0.5 * it * (double)th.Y[a];
+      }
+    }
+    A64[a][a] = diag;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r64[a][c] = (double)(r[a][c] * inv_s);
+  }
+  double J0[M][3];                       // one-sweep Jacobi estimate (before the elimination)
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) J0[a][c] = r64[a][c] / A64[a][a];
+  sm_eliminate<M, double>(A64, r64, J64);
+#pragma unroll
+  for (int k = 0; k < Dm::O; ++k)
+    tgt[n * Dm::O + k] = k < 3 * M ? (float)(J64[k / 3][k % 3] - J0[k / 3][k % 3]) : 0.0f;
 }
 
 }  // namespace lbm

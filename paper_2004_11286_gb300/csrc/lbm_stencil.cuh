@@ -78,10 +78,8 @@ __device__ __forceinline__ void load_state_moments(const DevParams<Real>& p, con
 // Stencil pass 1 (after a collision): G_alpha = c_omega d_alpha Phi_alpha (the
 // inner derivative of Eq. Xalpha) and K_alpha = s d_alpha C_p with s = c2 / theta;
 // the sender's theta is copied for the receivers' weights.
-template <class Real>
-__global__ void __launch_bounds__(BLOCK_LIGHT)
-grad_GK_kernel(const DevParams<Real> p, Real* __restrict__ side) {
-  const long long n = gtid();
+template <class Real, class G>
+__device__ __forceinline__ void grad_GK_node(const G& p, Real* __restrict__ side, long long n) {
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
@@ -107,10 +105,8 @@ grad_GK_kernel(const DevParams<Real> p, Real* __restrict__ side) {
 }
 
 // Stencil pass 2: X_alpha = -d_alpha G_alpha (Eq. Xalpha).
-template <class Real>
-__global__ void __launch_bounds__(BLOCK_LIGHT)
-grad_X_kernel(const DevParams<Real> p, Real* __restrict__ side) {
-  const long long n = gtid();
+template <class Real, class G>
+__device__ __forceinline__ void grad_X_node(const G& p, Real* __restrict__ side, long long n) {
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
@@ -127,6 +123,17 @@ grad_X_kernel(const DevParams<Real> p, Real* __restrict__ side) {
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) side[(SP_X + c) * N + n] = Real(-3) * d[c];
+}
+
+template <class Real>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+grad_GK_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+  grad_GK_node<Real>(p, side, gtid());
+}
+template <class Real>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+grad_X_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+  grad_X_node<Real>(p, side, gtid());
 }
 
 }  // namespace lbm

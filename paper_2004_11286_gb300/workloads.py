@@ -24,6 +24,9 @@ Recipes (stand-ins for the paper's experiments; lattice units, R_U = 1):
     trace-species diffusion velocities below sqrt(R_a T)).
   * ``random_mixture`` -- smooth random M-species field (sum of 16 Fourier
     modes per species), random molar masses and diffusivities.
+  * ``ensemble_shapes`` / ``ensemble_domain`` -- the batched ensemble: 64
+    ternary diffusion domains with edges uniform in 32..96, Dirichlet(1,1,1)
+    left/right compositions and log-uniform diffusivities.
 Common choices: T = 0.2 (inside the 0.2-0.5 range of Sec. 4.4); reference pressure P0 = T / m_mean with m_mean the
 molar mass of the domain-mean composition (reference density 1);
 mu_a = 0.1 P0, lambda_a = mu_a c_pa / 0.71
@@ -170,7 +173,11 @@ def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: floa
 
 
 def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
-                   shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0) -> Workload:
+                   shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0,
+                   field_seed: Optional[int] = None) -> Workload:
+    """Species constants (molar masses, C_v, diffusivities) from `seed`; the
+    initial fields from `field_seed` (default: the same generator, so one
+    seed fixes everything), so one mixture can be drawn in many states."""
     rng = np.random.Generator(np.random.PCG64(seed))
     nz, ny, nx = shape if shape is not None else (n, n, n)
     mm = rng.uniform(2.0, 44.0, size=M)
@@ -181,6 +188,8 @@ def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
             D[a, b] = D[b, a] = float(np.exp(rng.uniform(np.log(0.005), np.log(0.1))))
     if M == 1:
         D[0, 0] = 0.05
+    if field_seed is not None:
+        rng = np.random.Generator(np.random.PCG64(field_seed))
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     Xt = np.empty((M, nz, ny, nx))
     for a in range(M):
@@ -204,6 +213,45 @@ def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
     return Workload("random_mixture", mm, cv, D, mu, lam, X, u, T, P, steps)
 
 
+def ensemble_shapes(ndomains: int = 64, seed: int = 4, lo: int = 32, hi: int = 96):
+    """Grid shapes (nz, ny, nx) of the batched ensemble, each edge uniform in
+    lo..hi (mean domain about 3.3e5 nodes at the defaults)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [tuple(int(v) for v in rng.integers(lo, hi + 1, size=3)) for _ in range(ndomains)]
+
+
+def ensemble_domain(shape, seed: int, steps: int = 2000, width: float = 8.0,
+                    floor: float = 0.02) -> Workload:
+    """One ternary diffusion domain of the ensemble: m = 2, 40, 16, symmetric
+    D_ab log-uniform in [0.005, 0.1], left/right mole fractions drawn from
+    Dirichlet(1, 1, 1) (floored at `floor` and renormalised, so no species is
+    a trace in the tanh tails) joined by periodic tanh steps along x of scale
+    `width` (8 cells, as the ternary tube), uniform T and P, at rest."""
+    nz, ny, nx = shape
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mm = np.array([2.0, 40.0, 16.0])
+    cv = np.array([cv_for_mass(m) for m in mm])
+    D = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(a + 1, 3):
+            D[a, b] = D[b, a] = float(np.exp(rng.uniform(np.log(0.005), np.log(0.1))))
+    XL, XR = (np.maximum(rng.dirichlet(np.ones(3)), floor) for _ in range(2))
+    XL, XR = XL / XL.sum(), XR / XR.sum()
+    x = np.arange(nx, dtype=np.float64)
+    h = nx / 2.0
+    s = 0.5 * (np.tanh((x - (h - 0.5)) / width) - np.tanh((x - (nx - 0.5)) / width)
+               - np.tanh((x + 0.5) / width) + 1.0)
+    X = (1.0 - s)[None] * XL[:, None] + s[None] * XR[:, None]
+    X = np.broadcast_to(X[:, None, None, :], (3, nz, ny, nx)).copy()
+    X = X / X.sum(axis=0, keepdims=True)
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(X.reshape(3, -1).mean(axis=1), mm, T_AMBIENT)
+    P = np.full((nz, ny, nx), P0)
+    u = np.zeros((3, nz, ny, nx))
+    mu, lam = _transport(mm, cv, P0, 0.1)
+    return Workload("ensemble_domain", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
 def perturbation(shape, scale: float, seed: int) -> np.ndarray:
     """Seeded multiplicative noise (1 + scale * U(-1, 1)) used by tests to move
     a state off equilibrium; drawn here so both sides see the same numbers."""
@@ -219,3 +267,20 @@ def slaved_species(wl: Workload) -> int:
     Y = wl.X * mm
     Y = Y / Y.sum(axis=0, keepdims=True)
     return int(np.argmax(Y.reshape(wl.M, -1).min(axis=1)))
+
+
+def closure_initial_weights(M: int, seed: int = 0, hidden: int = 128) -> np.ndarray:
+    """Seeded initial weights of the closure network, packed W1 [H][F] | b1 |
+    W2 [H][H] | b2 | W3 [O][H] | b3 (F = pad16(4M + M(M-1)/2 + 1), O =
+    pad16(3M)): uniform in +-sqrt(6 / fan_in) (He), zero biases, and zero
+    rows of W3 on the padded outputs."""
+    def pad16(n):
+        return (n + 15) // 16 * 16
+    F, O = pad16(4 * M + M * (M - 1) // 2 + 1), pad16(3 * M)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W1 = rng.uniform(-1, 1, (hidden, F)) * np.sqrt(6.0 / F)
+    W2 = rng.uniform(-1, 1, (hidden, hidden)) * np.sqrt(6.0 / hidden)
+    W3 = rng.uniform(-1, 1, (O, hidden)) * np.sqrt(6.0 / hidden) * 0.1
+    W3[3 * M:] = 0.0
+    parts = [W1, np.zeros(hidden), W2, np.zeros(hidden), W3, np.zeros(O)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)

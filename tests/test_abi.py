@@ -74,7 +74,7 @@ def _params(M=2, **over):
 
 @pytest.mark.parametrize("field,value,status", [
     ("M", 0, 1), ("M", 9, 1), ("nx", 0, 1), ("R_U", 0.0, 1), ("precision", 7, 1),
-    ("coupling", 5, 1), ("closure", 3, 2), ("slaved_species", 4, 1),
+    ("coupling", 5, 1), ("closure", 3, 1), ("slaved_species", 4, 1),
 ])
 def test_create_rejects_bad_arguments_without_touching_cuda(built_library, field, value, status):
     from paper_2004_11286_gb300 import binding
@@ -85,6 +85,27 @@ def test_create_rejects_bad_arguments_without_touching_cuda(built_library, field
     assert st == status
     assert h.value is None
     assert lib.lbm_mix_last_error(None).decode()
+
+
+def test_closure_network_only_in_fp32_arithmetic(built_library):
+    # the learned closure runs in the FP32-arithmetic precisions with M >= 2
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    p, keep = _params(precision=0, closure=1)
+    h = ct.c_void_p()
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == 2
+    assert h.value is None
+
+
+def test_closure_sizes_match_the_oracle(built_library):
+    from paper_2004_11286_gb300 import binding
+    from oracle import closure as CL
+    for M in (1, 2, 3, 4, 8):
+        F, O, nw = binding.closure_sizes(M)
+        assert (F, O) == CL.closure_dims(M)[:2]
+        assert nw == CL.weight_count(M)
+    with pytest.raises(binding.LbmError):
+        binding.closure_sizes(5)
 
 
 def test_create_rejects_nonperiodic_and_asymmetric(built_library):

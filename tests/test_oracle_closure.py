@@ -51,8 +51,13 @@ def test_binary_targets_closed_form():
     itab = O.lbm_oracle.inv_tau_ab(st, prm)[0, 1].ravel()
     np.testing.assert_allclose(r[:, 0, :] + r[:, 1, :], 0, atol=1e-15)
     J1 = r[:, 0, :] / (1.0 + 0.5 * itab)[:, None] / s[:, None]
-    np.testing.assert_allclose(tgt[:, 0:3], J1, rtol=0, atol=1e-12)   # |targets| <= 1
-    np.testing.assert_allclose(tgt[:, 3:6], -J1, rtol=0, atol=1e-12)
+    # targets are the corrections to the Jacobi estimate r_a / (s A_aa), with
+    # A_11 = 1 + itab_12 Y_2 / 2 and A_22 = 1 + itab_12 Y_1 / 2
+    Y = st["Y"].reshape(2, -1)
+    J0_1 = r[:, 0, :] / s[:, None] / (1.0 + 0.5 * itab * Y[1])[:, None]
+    J0_2 = r[:, 1, :] / s[:, None] / (1.0 + 0.5 * itab * Y[0])[:, None]
+    np.testing.assert_allclose(tgt[:, 0:3], J1 - J0_1, rtol=0, atol=1e-12)   # |targets| <= 1
+    np.testing.assert_allclose(tgt[:, 3:6], -J1 - J0_2, rtol=0, atol=1e-12)
     assert np.all(tgt[:, 6:] == 0)
     # feature layout: X_a, r / s, h_12 / (1 + h_12) with h_12 = itab_12 / 2, 1, zeros
     np.testing.assert_allclose(feat[:, 0:2], st["X"].reshape(2, -1).T, rtol=1e-15)
@@ -68,13 +73,14 @@ def test_targets_solve_the_system(M):
     prm, st = _state(M, coupling="weak" if M == 3 else "strong")
     feat, tgt, s, A, r = CL.features_and_targets(st, prm)
     assert np.all(CL.residual(A, r, s, tgt, M) < 1e-13)
+    n = A.shape[0]
+    Jn = tgt[:, :3 * M].reshape(n, M, 3) + CL.jacobi_estimate(A, r / s[:, None, None])
     # sum_a J_a = 0 when sum_a r_a = 0 (columns of A - I sum to zero)
     if prm.coupling == "strong":
-        np.testing.assert_allclose(tgt[:, :3 * M].reshape(-1, M, 3).sum(axis=1), 0, atol=1e-13)
+        np.testing.assert_allclose(Jn.sum(axis=1), 0, atol=1e-13)
     # the species velocities of the oracle's own solve are J_a / rho_a
     V = O.sm_momenta(st, prm)
-    n = A.shape[0]
-    J = tgt[:, :3 * M].reshape(n, M, 3) * s[:, None, None]
+    J = Jn * s[:, None, None]
     np.testing.assert_allclose(J.transpose(1, 2, 0).reshape(V.shape),
                                V * st["rho_a"][:, None], rtol=1e-9, atol=1e-14)
 
