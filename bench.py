@@ -44,6 +44,12 @@ def _args():
     ap.add_argument("--n", type=int, default=128, help="grid edge of the acoustic-pulse workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["acoustic", "ensemble", "mixture"], default="acoustic",
+                    help="acoustic: the 128^3 binary pulse (default line); ensemble: 64 uneven ternary "
+                         "domains in one batched launch (BF16); mixture: M=8 192^3 random mixture, "
+                         "FP32 against BF16 + learned closure")
+    ap.add_argument("--no-chosen-form", action="store_true",
+                    help="skip the BF16-storage / learned-closure comparison on the same workload")
     ap.add_argument("--oracle-sample", nargs=2, type=int, metavar=("EDGE", "STEPS"),
                     help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -200,6 +206,180 @@ def _algorithmic_bytes(M: int, precision: str):
 
 
 # ---------------------------------------------------------------------------
+# The chosen form on the same workload: BF16-stored populations, then BF16
+# plus the learned Stefan-Maxwell closure (network trained here on pairs the
+# exact method generates from this workload, exact fallback).
+# ---------------------------------------------------------------------------
+def _chosen_form(wl, dev, steps: int, peak: float):
+    import torch
+    from paper_2004_11286_gb300 import binding, workloads as W
+    slaved = W.slaved_species(wl)
+    N = wl.nodes
+    out = {}
+
+    def timed(h, k):
+        h.init_fields(wl.X, wl.u, wl.T, wl.P)
+        h.step(5)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(h.stream)
+        h.step(k)
+        e1.record(h.stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    alg = _algorithmic_bytes(wl.M, "bf16")["step"]
+    hb = binding.from_workload(wl, precision="bf16", slaved=slaved, device=dev)
+    ms = timed(hb, steps)
+    hb.close()
+    out["bf16"] = {"MLUPS": round(N / ms / 1e3, 2), "ms_per_step": round(ms, 5),
+                   "step_frac": round(alg * N / (ms * 1e-3) / 1e9 / peak, 4)}
+    # training pairs from the exact method on this workload, then Adam
+    t0 = time.perf_counter()
+    hs = binding.from_workload(wl, precision="fp32", slaved=slaved, device=dev)
+    hs.init_fields(wl.X, wl.u, wl.T, wl.P)
+    feats, tgts = [], []
+    for _ in range(3):
+        hs.step(20)
+        f, g = hs.closure_samples()
+        idx = torch.randperm(N, generator=torch.Generator().manual_seed(len(feats)))[: min(N, 1 << 18)].to(dev)
+        feats.append(f[idx])
+        tgts.append(g[idx])
+    hs.close()
+    feat = torch.cat(feats).contiguous()
+    tgt = torch.cat(tgts).contiguous()
+    hm = binding.from_workload(wl, precision="bf16", slaved=slaved, closure="mlp", device=dev)
+    hm.set_closure_weights(W.closure_initial_weights(wl.M, seed=1))
+    loss = None
+    for k, lr in ((3000, 1e-3), (1500, 2e-4)):
+        loss = hm.closure_train(feat, tgt, batch=4096, steps=k, lr=lr)
+    train_s = time.perf_counter() - t0
+    hm.closure_stats(reset=True)
+    ms = timed(hm, max(50, steps // 4))
+    acc, fb = hm.closure_stats()
+    hm.close()
+    out["bf16_learned_closure"] = {
+        "MLUPS": round(N / ms / 1e3, 2), "ms_per_step": round(ms, 5),
+        "step_frac": round(alg * N / (ms * 1e-3) / 1e9 / peak, 4),
+        "accepted_fraction": round(acc / max(1, acc + fb), 5), "residual_bound": 1e-2,
+        "train": {"pairs": int(feat.shape[0]), "adam_steps": 4500, "last_loss": loss, "seconds": round(train_s, 2)}}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Secondary workloads (not the default line): the batched ensemble and the
+# eight-species mixture.
+# ---------------------------------------------------------------------------
+def _timed_steps(step, stream, k):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _bench_ensemble(a, dev):
+    from paper_2004_11286_gb300 import binding, workloads as W
+    shapes = W.ensemble_shapes(64, seed=4)
+    kws, wls = [], []
+    for k, sh in enumerate(shapes):
+        wl = W.ensemble_domain(sh, 100 + k)
+        kws.append(binding.workload_params(wl, precision="bf16", slaved=W.slaved_species(wl)))
+    b = binding.LbmBatch(kws, device=dev)
+    for k, sh in enumerate(shapes):
+        wl = W.ensemble_domain(sh, 100 + k)
+        b.domain(k).init_fields(wl.X, wl.u, wl.T, wl.P)
+    cfg = b.autotune(trial_steps=3)
+    b.step(a.warmup)
+    b.synchronize()
+    clocks = ClockSampler(_physical_gpu_index(0))
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    ms = _timed_steps(b.step, b.stream, a.steps)
+    clocks.mark(t0, time.perf_counter())
+    b.synchronize()
+    clk = clocks.stop()
+    N = b.nodes
+    value = N * a.steps / (ms * 1e-3) / 1e6
+    peak, src = _peaks()
+    alg = _algorithmic_bytes(3, "bf16")["step"]
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "batched ensemble: 64 ternary diffusion domains, edges uniform in 32..96 "
+                                   f"({N} nodes), M=3 (m=2,40,16), BF16 storage, FP32 arithmetic, one launch "
+                                   "per kernel for all domains, step pairs as a CUDA graph",
+                       "autotuned": cfg, "l2": "inputs larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "step_frac": round(alg * N * a.steps / (ms * 1e-3) / 1e9 / peak, 4),
+                         "peak": peak, "unit": "GB/s", "step_algorithmic_bytes_per_node": alg},
+            "clocks": clk}
+    b.close()
+    return line
+
+
+def _bench_mixture(a, dev):
+    import torch
+    from paper_2004_11286_gb300 import binding, workloads as W
+    wl = W.random_mixture(M=8, n=192, seed=7)
+    slaved = W.slaved_species(wl)
+    N = wl.nodes
+    peak, src = _peaks()
+    out = {}
+    h = binding.from_workload(wl, precision="fp32", slaved=slaved, device=dev)
+    h.init_fields(wl.X, wl.u, wl.T, wl.P)
+    h.step(a.warmup)
+    feats, tgts = [], []
+    for _ in range(3):
+        h.step(20)
+        f, g = h.closure_samples()
+        idx = torch.randperm(N, generator=torch.Generator().manual_seed(len(feats)))[: 1 << 18].to(dev)
+        feats.append(f[idx])
+        tgts.append(g[idx])
+    ms = _timed_steps(h.step, h.stream, a.steps)
+    h.close()
+    alg32 = _algorithmic_bytes(8, "fp32")["step"]
+    out["fp32"] = {"MLUPS": round(N * a.steps / ms / 1e3, 2), "ms_per_step": round(ms / a.steps, 4),
+                   "step_frac": round(alg32 * N * a.steps / (ms * 1e-3) / 1e9 / peak, 4)}
+    alg16 = _algorithmic_bytes(8, "bf16")["step"]
+    hb = binding.from_workload(wl, precision="bf16", slaved=slaved, device=dev)
+    hb.init_fields(wl.X, wl.u, wl.T, wl.P)
+    hb.step(a.warmup)
+    ms = _timed_steps(hb.step, hb.stream, a.steps)
+    hb.close()
+    out["bf16"] = {"MLUPS": round(N * a.steps / ms / 1e3, 2), "ms_per_step": round(ms / a.steps, 4),
+                   "step_frac": round(alg16 * N * a.steps / (ms * 1e-3) / 1e9 / peak, 4)}
+    feat = torch.cat(feats).contiguous()
+    tgt = torch.cat(tgts).contiguous()
+    hm = binding.from_workload(wl, precision="bf16", slaved=slaved, closure="mlp", device=dev)
+    hm.set_closure_weights(W.closure_initial_weights(8, seed=1))
+    t0 = time.perf_counter()
+    for k, lr in ((4000, 1e-3), (2000, 2e-4)):
+        loss = hm.closure_train(feat, tgt, batch=4096, steps=k, lr=lr)
+    train_s = time.perf_counter() - t0
+    hm.init_fields(wl.X, wl.u, wl.T, wl.P)
+    hm.step(a.warmup)
+    hm.closure_stats(reset=True)
+    ms = _timed_steps(hm.step, hm.stream, a.steps)
+    acc, fb = hm.closure_stats()
+    hm.close()
+    out["bf16_learned_closure"] = {"MLUPS": round(N * a.steps / ms / 1e3, 2), "ms_per_step": round(ms / a.steps, 4),
+                                   "step_frac": round(alg16 * N * a.steps / (ms * 1e-3) / 1e9 / peak, 4),
+                                   "accepted_fraction": round(acc / max(1, acc + fb), 5),
+                                   "train": {"pairs": int(feat.shape[0]), "adam_steps": 6000, "last_loss": loss,
+                                             "seconds": round(train_s, 2)}}
+    line = {"metric": METRIC, "value": out["fp32"]["MLUPS"], "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "random 8-species mixture, 192^3 periodic, smooth 16-mode composition field, "
+                                   "m_a in [2,44], D_ab log-uniform in [0.005, 0.1]"},
+            "chosen_form": out}
+    return line
+
+
+# ---------------------------------------------------------------------------
 def main():
     a = _args()
     if a.oracle_sample:
@@ -246,6 +426,11 @@ def main():
     if world > 1:
         dist.barrier()
     binding.load_library()
+    if a.workload != "acoustic":
+        line = _bench_ensemble(a, dev) if a.workload == "ensemble" else _bench_mixture(a, dev)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     wl = W.acoustic_pulse(n=a.n)
     slaved = W.slaved_species(wl)
@@ -340,6 +525,10 @@ def main():
                "note": "init_fields from pinned host fields + step(K) + get_moments to pinned host + "
                        "diagnostics, host wall clock"}
 
+    chosen = None
+    if not a.no_chosen_form and a.precision == "fp32":
+        chosen = _chosen_form(wl, dev, min(a.steps, 500), peak)
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
         try:
@@ -359,6 +548,7 @@ def main():
                                  (27 * (wl.M + 2) * N * {"fp64": 8, "fp32": 4}.get(a.precision, 2) / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "chosen_form": chosen,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     h.close()

@@ -41,22 +41,79 @@ constexpr int collide_min_blocks() {
   return LBM_COLLIDE_MINB < fit ? LBM_COLLIDE_MINB : fit;
 }
 
+// Bulk (TMA engine) row loads of the populations where the grid allows them,
+// from LBM_COLLIDE_BULK_MIN_M species: measured on GB300 (128^3 random
+// mixtures) M = 3 FP32 2585 against 2301 MLUPS for register loads, M = 8
+// 635 against 576, but M = 2 3464 against 3566 (the 128^3 acoustic pulse).
+#ifndef LBM_COLLIDE_BULK
+#define LBM_COLLIDE_BULK 1
+#endif
+#ifndef LBM_COLLIDE_BULK_MIN_M
+#define LBM_COLLIDE_BULK_MIN_M 3
+#endif
+
+// Species counts from which the species update loops over the velocities at
+// run time rather than unrolled (see the species phase of collide_node).
+#ifndef LBM_SPECIES_LOOP_MIN_M
+#define LBM_SPECIES_LOOP_MIN_M 4
+#endif
+
 template <int M, class Real, int CL = 0>
 constexpr size_t collide_stage_bytes() {
   return (size_t)(M + 2) * Q * collide_block<M, Real, CL>() * sizeof(Real);
 }
-template <int M, class Real, int CL = 0>
+// Bulk row loads (LD = 1) add one halo value per staged plane and an mbarrier.
+template <int M, class Real>
+constexpr size_t collide_halo_bytes() {
+  return ((size_t)(M + 2) * Q * sizeof(Real) + 7) / 8 * 8;
+}
+template <int M, class Real, int CL = 0, int LD = 0>
 constexpr size_t collide_smem() {
   if constexpr (CL) return collide_stage_bytes<M, Real, CL>() + MlpDims<M>::SMEM;
+  if constexpr (LD) return collide_stage_bytes<M, Real, CL>() + collide_halo_bytes<M, Real>() + 8;
   return collide_stage_bytes<M, Real, CL>();
 }
 // The network closure exists for the FP32-arithmetic paths with M >= 2.
 template <int M, class Real>
 constexpr bool kMlpOk = (M >= 2) && sizeof(Real) == 4;
 
+// Bulk row loads of the row segment [x0, x0 + BS) whose first node is n0:
+// every lattice plane of every velocity as one aligned copy of BS values of
+// its source row (the segment's own row at even parity, the row y - c_y,
+// z - c_z at odd parity) into buf[plane][BS], completing on mbar (armed by
+// the caller); at odd parity on segmented rows the value each x-shifted
+// velocity needs from outside the segment goes to halo[plane].  Planes are
+// shared out over lanes lane, lane + nlanes, ...
+template <int M, class Real, class Store, int PAR, int BS>
+__device__ __forceinline__ void issue_row_loads(const DevParams<Real>& p, const Store* __restrict__ pops, Real* buf,
+                                                Real* halo, uint32_t mbar, long long n0, int lane, int nlanes) {
+  const long long N = p.N;
+  const long long rowi = n0 / p.nx;
+  const int x0 = (int)(n0 - rowi * p.nx);
+  const int yr = (int)(rowi % p.ny), zr0 = (int)(rowi / p.ny);
+  const bool whole_row = p.nx == BS;
+  for (int k = lane; k < (M + 2) * Q; k += nlanes) {
+    const int L = k / Q, i = k % Q;
+    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+    int ys = yr, zs = zr0, slot = i;
+    if (PAR) {
+      ys = yr - cy; ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+      zs = zr0 - cz; zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+      slot = Q - 1 - i;
+    }
+    const Store* src = pops + ((long long)(L * Q + slot) * N + ((long long)zs * p.ny + ys) * p.nx);
+    bulk_g2s(buf + (size_t)k * BS, src + x0, (uint32_t)(BS * sizeof(Real)), mbar);
+    if (PAR && cx != 0 && !whole_row) {
+      int xh = cx > 0 ? x0 - 1 : x0 + BS;
+      xh = xh < 0 ? xh + p.nx : (xh >= p.nx ? xh - p.nx : xh);
+      halo[k] = (Real)src[xh];
+    }
+  }
+}
+
 // One node's collide + stream (thread threadIdx.x of the block; the block's
 // shared memory holds the stage and, with CL = 1, the network's tile).
-template <int M, class Real, class Store, int PAR, int CL>
+template <int M, class Real, class Store, int PAR, int CL, int LD = 0>
 __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __restrict__ pops,
                                              Real* __restrict__ side, unsigned* __restrict__ err,
                                              const unsigned char* __restrict__ mlp_img,
@@ -86,24 +143,32 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   Real rhoE_dev = Real(0), q[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
   for (int a = 0; a < M; ++a) { rdev[a] = Real(0); ja[a][0] = ja[a][1] = ja[a][2] = Real(0); }
-  static_for<0, Q>([&](auto I_) {
+  // The staged value of lattice L, velocity i (cx its x component) for this
+  // thread.  With bulk row loads at odd parity a velocity's source row sits
+  // in the stage shifted by cx; the value that falls outside the segment is
+  // the plane's halo value (or wraps, when the segment is the whole row).
+  Real* const halo = sm + (M + 2) * Q * BS;
+  const bool whole_row = p.nx == BS;
+  auto cell = [&](int L, int i, int cx) -> Real& {
+    if constexpr (LD && PAR) {
+      const int li = tid - cx;
+      if (li < 0 || li >= BS) return whole_row ? sm[(L * Q + i) * BS + (li < 0 ? BS - 1 : 0)] : halo[L * Q + i];
+      return sm[(L * Q + i) * BS + li];
+    } else {
+      (void)cx;
+      return sm[(L * Q + i) * BS + tid];
+    }
+  };
+  auto accumulate = [&](auto I_, const Real (&v)[M], Real fv, Real gv) {
     constexpr int i = decltype(I_)::value;
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-    long long node; int slot;
-    aa_read_loc(PAR, nb, n, i, node, slot);
-    Real cf = Real(0), cg = Real(0);
-    if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx, -cy, -cz), cf, cg);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
-      sm[(a * Q + i) * BS + tid] = v;
-      rdev[a] += v;
-      if (cx) ja[a][0] += cx * v;
-      if (cy) ja[a][1] += cy * v;
-      if (cz) ja[a][2] += cz * v;
+      rdev[a] += v[a];
+      if (cx) ja[a][0] += cx * v[a];
+      if (cy) ja[a][1] += cy * v[a];
+      if (cz) ja[a][2] += cz * v[a];
     }
-    const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
-    sm[(M * Q + i) * BS + tid] = fv;
     rho_dev += fv;
     if (cx) { j[0] += cx * fv; S[0] += fv; }
     if (cy) { j[1] += cy * fv; S[1] += fv; }
@@ -111,13 +176,66 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     if (cx && cy) S[3] += (cx * cy) * fv;
     if (cx && cz) S[4] += (cx * cz) * fv;
     if (cy && cz) S[5] += (cy * cz) * fv;
-    const Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
-    sm[((M + 1) * Q + i) * BS + tid] = gv;
     rhoE_dev += gv;
     if (cx) q[0] += cx * gv;
     if (cy) q[1] += cy * gv;
     if (cz) q[2] += cz * gv;
-  });
+  };
+  if constexpr (LD) {
+    // The block is the row segment [x0, x0 + BS) of one grid row.  Every
+    // lattice plane of every velocity arrives as one aligned bulk copy of the
+    // BS values of its source row (the node's own row at even parity, the
+    // row y - c_y, z - c_z at odd parity); the senders' deferred terms are
+    // gathered while the copies are in flight.
+    const uint32_t mbar = smem_u32(reinterpret_cast<unsigned char*>(halo) + collide_halo_bytes<M, Real>());
+    if (tid == 0) {
+      mbar_init(mbar, 1);
+      mbar_expect_tx(mbar, (uint32_t)((M + 2) * Q * BS * sizeof(Real)));
+    }
+    __syncthreads();
+    issue_row_loads<M, Real, Store, PAR, BS>(p, pops, sm, halo, mbar, n_raw - tid, tid, BS);
+    Real cfv[Q], cgv[Q];
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      cfv[i] = Real(0); cgv[i] = Real(0);
+      if constexpr (i != 13)
+        incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cfv[i], cgv[i]);
+    });
+    if (!mbar_wait(mbar, 0u)) atomicOr(err, 4u);
+    __syncthreads();                                   // halo values
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      constexpr int cx = cx_of(i);
+      Real v[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) v[a] = cell(a, i, cx);
+      Real& fc = cell(M, i, cx);
+      Real& gc = cell(M + 1, i, cx);
+      Real fv = fc, gv = gc;
+      if constexpr (c2_of(i) == 1) { fv += cfv[i]; fc = fv; }
+      if constexpr (i != 13) { gv += cgv[i]; gc = gv; }
+      accumulate(I_, v, fv, gv);
+    });
+  } else {
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      long long node; int slot;
+      aa_read_loc(PAR, nb, n, i, node, slot);
+      Real cf = Real(0), cg = Real(0);
+      if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cf, cg);
+      Real v[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        v[a] = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+        sm[(a * Q + i) * BS + tid] = v[a];
+      }
+      const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+      sm[(M * Q + i) * BS + tid] = fv;
+      const Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+      sm[((M + 1) * Q + i) * BS + tid] = gv;
+      accumulate(I_, v, fv, gv);
+    });
+  }
 
   // a3: coupling + thermodynamics
   Real jsum[3] = {Real(0), Real(0), Real(0)};
@@ -248,13 +366,13 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         aa_write_loc(PAR, nbw, n, i, node, slot);
         const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
         s_f += e;
-        const Real fv = sm[(M * Q + i) * BS + tid];
+        const Real fv = cell(M, i, cx_of(i));
         if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * (e - fv));
       }
     });
     long long node; int slot;
     aa_write_loc(PAR, nbw, n, 13, node, slot);
-    const Real fv = sm[(M * Q + 13) * BS + tid];
+    const Real fv = cell(M, 13, 0);
     if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
   }
 
@@ -334,7 +452,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         const Real dwi = dx * wy * wz + rx * dy * wz + rx * ry * dz;
         const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
         s_g += e;
-        const Real gv = sm[((M + 1) * Q + i) * BS + tid];
+        const Real gv = cell(M + 1, i, cx);
         if (active)
           codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
                                    gv + om * (e - gv) + wi * dotc<Real, i>(mvec));
@@ -342,7 +460,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     });
     long long node; int slot;
     aa_write_loc(PAR, nbw, n, 13, node, slot);
-    const Real gv = sm[((M + 1) * Q + 13) * BS + tid];
+    const Real gv = cell(M + 1, 13, 0);
     if (active)
       codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
   }
@@ -374,48 +492,77 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 #pragma unroll
     for (int a = 0; a < M; ++a) { s_e[a] = Real(0); s_F[a] = Real(0); }
     const Nbr nbw = opaque(nb);
-    static_for<0, Q>([&](auto I_) {
-      constexpr int i = decltype(I_)::value;
-      if constexpr (i != 13) {
-        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        long long node; int slot;
-        aa_write_loc(PAR, nbw, n, i, node, slot);
-        Real Dif[M];
+    // One velocity of the species update.  With many species the velocity
+    // loop runs at run time: unrolled, the compiler keeps every species' axis
+    // factors of all 26 velocities live at once and spills.
+    auto species_velocity = [&](int i, int cx, int cy, int cz, long long node, int slot) {
+      Real Dif[M];
 #pragma unroll
-        for (int b = 0; b < M; ++b) {
-          // a = Psi(u), s = Psi(u + V) per axis; Dif = a_x a_y a_z - s_x s_y s_z
-          const Real z = zr[b] + dz[b];
-          const Real ax = pf_a<Real>(cx, th.u_sp[0], x2[0], z);
-          const Real ay = pf_a<Real>(cy, th.u_sp[1], x2[1], z);
-          const Real az = pf_a<Real>(cz, th.u_sp[2], x2[2], z);
-          const Real tx = pf_v<Real>(cx, V[b][0], ev[b][0]);
-          const Real ty = pf_v<Real>(cy, V[b][1], ev[b][1]);
-          const Real tz = pf_v<Real>(cz, V[b][2], ev[b][2]);
-          const Real sx = ax - tx, sy = ay - ty;
-          Dif[b] = th.rho_a[b] * (tx * ay * az + sx * ty * az + sx * sy * tz);
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-          Real F = Real(0);
-#pragma unroll
-          for (int b = 0; b < M; ++b) F += p.Cab[a][b] * Dif[b];
-          F *= tY[a];
-          const Real e = th.rho_a[a] * pf_diff<Real, i>(th.u_sp, x2, zr[a], dz[a])
-                       + th.rho_a_dev[a] * pf_ref<Real, i>(zr[a]);
-          s_e[a] += e; s_F[a] += F;
-          const Real kv = sm[(a * Q + i) * BS + tid];
-          if (active)
-            codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
-                                     kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
-        }
+      for (int b = 0; b < M; ++b) {
+        // a = Psi(u), s = Psi(u + V) per axis; Dif = a_x a_y a_z - s_x s_y s_z
+        const Real z = zr[b] + dz[b];
+        const Real ax = pf_a<Real>(cx, th.u_sp[0], x2[0], z);
+        const Real ay = pf_a<Real>(cy, th.u_sp[1], x2[1], z);
+        const Real az = pf_a<Real>(cz, th.u_sp[2], x2[2], z);
+        const Real tx = pf_v<Real>(cx, V[b][0], ev[b][0]);
+        const Real ty = pf_v<Real>(cy, V[b][1], ev[b][1]);
+        const Real tz = pf_v<Real>(cz, V[b][2], ev[b][2]);
+        const Real sx = ax - tx, sy = ay - ty;
+        Dif[b] = th.rho_a[b] * (tx * ay * az + sx * ty * az + sx * sy * tz);
       }
-    });
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        Real F = Real(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) F += p.Cab[a][b] * Dif[b];
+        F *= tY[a];
+        // Psi_i(u, zr + dz) - Psi_i(0, zr), telescoped over the axes
+        const Real zz = zr[a] + dz[a];
+        const Real rx = pf_r<Real>(cx, zr[a]), ry = pf_r<Real>(cy, zr[a]);
+        const Real d = pf_da<Real>(cx, th.u_sp[0], x2[0], dz[a]) * pf_a<Real>(cy, th.u_sp[1], x2[1], zz)
+                           * pf_a<Real>(cz, th.u_sp[2], x2[2], zz)
+                     + rx * pf_da<Real>(cy, th.u_sp[1], x2[1], dz[a]) * pf_a<Real>(cz, th.u_sp[2], x2[2], zz)
+                     + rx * ry * pf_da<Real>(cz, th.u_sp[2], x2[2], dz[a]);
+        const Real e = th.rho_a[a] * d + th.rho_a_dev[a] * (rx * ry * pf_r<Real>(cz, zr[a]));
+        s_e[a] += e; s_F[a] += F;
+        const Real kv = cell(a, i, cx);
+        if (active)
+          codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
+                                   kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
+      }
+    };
+    if constexpr (M >= LBM_SPECIES_LOOP_MIN_M) {
+#pragma unroll 1
+      for (int i = 0; i < Q; ++i) {
+        if (i == 13) continue;
+        const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+        long long node; int slot;
+        if (PAR == 0) {
+          node = n; slot = Q - 1 - i;
+        } else {
+          const unsigned xs = cx < 0 ? nbw.xs[0] : (cx > 0 ? nbw.xs[2] : nbw.xs[1]);
+          const unsigned ys = cy < 0 ? nbw.ys[0] : (cy > 0 ? nbw.ys[2] : nbw.ys[1]);
+          const unsigned zs = cz < 0 ? nbw.zs[0] : (cz > 0 ? nbw.zs[2] : nbw.zs[1]);
+          node = (long long)(zs + ys + xs); slot = i;
+        }
+        species_velocity(i, cx, cy, cz, node, slot);
+      }
+    } else {
+      static_for<0, Q>([&](auto I_) {
+        constexpr int i = decltype(I_)::value;
+        if constexpr (i != 13) {
+          long long node; int slot;
+          aa_write_loc(PAR, nbw, n, i, node, slot);
+          species_velocity(i, cx_of(i), cy_of(i), cz_of(i), node, slot);
+        }
+      });
+    }
     long long node; int slot;
     aa_write_loc(PAR, nbw, n, 13, node, slot);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];
-      const Real kv = sm[(a * Q + 13) * BS + tid];
+      const Real kv = cell(a, 13, 0);
       if (active)
         codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
                                  kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
@@ -424,13 +571,15 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   if constexpr (CL) mlp.teardown();
 }
 
-template <int M, class Real, class Store, int PAR, int CL = 0>
+// LD = 1: bulk row loads; needs Store == Real, nx a multiple of the block
+// size and a grid whose blocks are whole row segments (checked by the host).
+template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0>
 __global__ void __launch_bounds__(collide_block<M, Real, CL>(), collide_min_blocks<M, Real, CL>())
 collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
                unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
                unsigned long long* __restrict__ mlp_stats) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  collide_node<M, Real, Store, PAR, CL>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
+  collide_node<M, Real, Store, PAR, CL, LD>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
 }
 
 }  // namespace lbm

@@ -178,22 +178,36 @@ struct Launch {
         *c.p64, (Store*)c.pops, c.base, X, u, T, Pr);
     return cudaGetLastError();
   }
-  template <int CL>
-  static void collide(const LaunchCtx& c, int parity, Real* side) {
+  template <int CL, int LD>
+  static void collide_launch(const LaunchCtx& c, int parity, Real* side) {
     constexpr int BS = collide_block<M, Real, CL>();
-    constexpr size_t smem = collide_smem<M, Real, CL>();
+    constexpr size_t smem = collide_smem<M, Real, CL, LD>();
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1, CL, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
       attr = true;
     }
     if (parity == 0)
-      collide_kernel<M, Real, Store, 0, CL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+      collide_kernel<M, Real, Store, 0, CL, LD><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
           P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
     else
-      collide_kernel<M, Real, Store, 1, CL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+      collide_kernel<M, Real, Store, 1, CL, LD><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
           P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
+  }
+  // Bulk row loads where the blocks are whole row segments and the stage
+  // holds the stored type (FP64, FP32).
+  template <int CL>
+  static void collide(const LaunchCtx& c, int parity, Real* side) {
+    if constexpr (CL == 0 && LBM_COLLIDE_BULK && M >= LBM_COLLIDE_BULK_MIN_M && std::is_same<Real, Store>::value) {
+      if (P(c).nx % collide_block<M, Real>() == 0) {
+        collide_launch<0, 1>(c, parity, side);
+        return;
+      }
+    }
+    collide_launch<CL, 0>(c, parity, side);
   }
   static cudaError_t step(const LaunchCtx& c, int parity) {
     Real* side = (Real*)c.side;

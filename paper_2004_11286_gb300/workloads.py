@@ -174,10 +174,12 @@ def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: floa
 
 def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
                    shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0,
-                   field_seed: Optional[int] = None) -> Workload:
+                   field_seed: Optional[int] = None, amplitude: float = 0.5) -> Workload:
     """Species constants (molar masses, C_v, diffusivities) from `seed`; the
     initial fields from `field_seed` (default: the same generator, so one
-    seed fixes everything), so one mixture can be drawn in many states."""
+    seed fixes everything), so one mixture can be drawn in many states.
+    Mole fractions are max(0.05, 1 + amplitude * phi) renormalised, with phi
+    the normalised sum of Fourier modes."""
     rng = np.random.Generator(np.random.PCG64(seed))
     nz, ny, nx = shape if shape is not None else (n, n, n)
     mm = rng.uniform(2.0, 44.0, size=M)
@@ -201,7 +203,7 @@ def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
             phi += A * np.cos(2.0 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ps)
         mx = np.abs(phi).max()
         phi = phi / mx if mx > 0 else phi
-        Xt[a] = np.maximum(0.05, 1.0 + 0.5 * phi)
+        Xt[a] = np.maximum(0.05, 1.0 + amplitude * phi)
     X = Xt / Xt.sum(axis=0, keepdims=True)
     T = np.full((nz, ny, nx), T_AMBIENT)
     P0 = _p0(X.reshape(M, -1).mean(axis=1), mm, T_AMBIENT)
