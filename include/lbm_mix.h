@@ -293,19 +293,28 @@ LBM_API long long lbm_mix_batch_nodes(lbm_mix_batch_t b);
  * step count).  Asynchronous on the caller's stream. */
 LBM_API lbm_status lbm_mix_batch_step(lbm_mix_batch_t b, int nsteps);
 
-/* Times the candidate launch shapes (collide grid: one block per tile or 1-4
- * blocks per SM, persistent; stencil blocks of 128 or 256 threads, one per
- * tile or 8/16 per SM) on `trial_steps` steps each, keeps the fastest and
- * restores the state it started from.  config (may be NULL) receives
- * [collide grid, stencil block, stencil grid]; *best_ms the step time. */
+/* Times the candidate execution plans on `trial_steps` steps each (graph
+ * replays), keeps the fastest and restores the state it started from:
+ *   mode 0, persistent launches over the tiles of all domains (collide grid:
+ *     one block per tile or 1-4 blocks per SM; stencil blocks of 128 or 256
+ *     threads, one per tile or 8/16 per SM);
+ *   mode 1, each domain's own kernels (its parameter block by value) on 4, 8
+ *     or 16 concurrent branches of the step graph.
+ * config (may be NULL) receives [collide grid, stencil block, stencil grid,
+ * mode, branches]; *best_ms the step time. */
 LBM_API lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* config, double* best_ms);
 
 /* Sets the launch shapes by hand; use_graph = 0 launches every step. */
 LBM_API lbm_status lbm_mix_batch_set_config(lbm_mix_batch_t b, int grid_collide, int block_stencil,
                                             int grid_stencil, int use_graph);
 
-/* config[8]: collide grid, stencil block, stencil grid, graphs on, collide
- * tiles, 128-thread tiles, 256-thread tiles, nodes per collide tile. */
+/* Chooses the execution plan by hand (mode 0 or 1 as in
+ * lbm_mix_batch_autotune, 1..64 graph branches for mode 1). */
+LBM_API lbm_status lbm_mix_batch_set_mode(lbm_mix_batch_t b, int mode, int branches);
+
+/* config[10]: collide grid, stencil block, stencil grid, graphs on, collide
+ * tiles, 128-thread tiles, 256-thread tiles, nodes per collide tile, mode,
+ * branches. */
 LBM_API lbm_status lbm_mix_batch_config(lbm_mix_batch_t b, int* config);
 
 /* Waits for the batch and reports a non-physical node (LBM_ERR_NONFINITE). */

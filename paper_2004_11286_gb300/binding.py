@@ -79,6 +79,7 @@ SIGNATURES = {
     "lbm_mix_batch_step": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "lbm_mix_batch_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), _DP]),
     "lbm_mix_batch_set_config": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int]),
+    "lbm_mix_batch_set_mode": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int]),
     "lbm_mix_batch_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "lbm_mix_batch_synchronize": (ct.c_int, [ct.c_void_p]),
     "lbm_mix_batch_destroy": (ct.c_int, [ct.c_void_p]),
@@ -440,21 +441,25 @@ class LbmBatch:
     def step(self, n: int = 1):
         self._check(self.lib.lbm_mix_batch_step(self.b, int(n)))
 
-    def autotune(self, trial_steps: int = 3):
-        cfg = (ct.c_int * 3)()
+    def autotune(self, trial_steps: int = 4):
+        cfg = (ct.c_int * 5)()
         ms = ct.c_double()
         self._check(self.lib.lbm_mix_batch_autotune(self.b, int(trial_steps), cfg, ct.byref(ms)))
-        return dict(grid_collide=cfg[0], block_stencil=cfg[1], grid_stencil=cfg[2], ms_per_step=ms.value)
+        return dict(grid_collide=cfg[0], block_stencil=cfg[1], grid_stencil=cfg[2], mode=cfg[3], branches=cfg[4],
+                    ms_per_step=ms.value)
+
+    def set_mode(self, mode: int, branches: int = 8):
+        self._check(self.lib.lbm_mix_batch_set_mode(self.b, int(mode), int(branches)))
 
     def set_config(self, grid_collide: int, block_stencil: int, grid_stencil: int, use_graph: bool = True):
         self._check(self.lib.lbm_mix_batch_set_config(self.b, int(grid_collide), int(block_stencil),
                                                       int(grid_stencil), int(bool(use_graph))))
 
     def config(self):
-        c = (ct.c_int * 8)()
+        c = (ct.c_int * 10)()
         self._check(self.lib.lbm_mix_batch_config(self.b, c))
         keys = ("grid_collide", "block_stencil", "grid_stencil", "use_graph", "tiles_collide", "tiles_128",
-                "tiles_256", "collide_block")
+                "tiles_256", "collide_block", "mode", "branches")
         return dict(zip(keys, list(c)))
 
     def synchronize(self):

@@ -372,6 +372,13 @@ struct lbm_mix_batch {
   std::vector<long long> uploaded;   // parameter versions on the device
   cudaGraphExec_t graph = nullptr;
   bool use_graph = true;
+  // mode 0: persistent launches over the tiles of all domains;
+  // mode 1: each domain's own kernels, domains spread over `nbranch`
+  //         concurrent branches of the graph.
+  int mode = 0, nbranch = 8;
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
   long long steps = 0, nodes = 0;
   std::string err;
 
@@ -407,22 +414,68 @@ struct lbm_mix_batch {
     }
     return cuda(cudaStreamSynchronize(stream), "synchronize");   // the host blocks must stay valid
   }
+  // One domain's step (its own kernels, parameter block by value) on stream s.
+  cudaError_t domain_step(int d, cudaStream_t s, int parity) {
+    lbm::LaunchCtx c = dom[d]->ctx();
+    c.stream = s;
+    return ks->step(c, parity);
+  }
+  lbm_status ensure_branches() {
+    if ((int)branches.size() >= nbranch) return LBM_OK;
+    if (!fork && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+      return fail(LBM_ERR_CUDA, "event creation failed");
+    while ((int)branches.size() < nbranch) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(LBM_ERR_CUDA, "stream creation failed");
+      branches.push_back(s);
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LBM_ERR_CUDA, "event creation failed");
+      joins.push_back(e);
+    }
+    return LBM_OK;
+  }
   lbm_status build_graph() {
     drop_graph();
+    if (mode == 1) {
+      lbm_status st = ensure_branches();
+      if (st != LBM_OK) return st;
+    }
     cudaGraph_t g = nullptr;
     lbm_status st = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (st != LBM_OK) return st;
-    const lbm::BatchCtx c = ctx();
-    cudaError_t e0 = ks->batch_step(c, 0);
-    cudaError_t e1 = ks->batch_step(c, 1);
+    cudaError_t e = cudaSuccess;
+    if (mode == 0) {
+      const lbm::BatchCtx c = ctx();
+      e = ks->batch_step(c, 0);
+      if (e == cudaSuccess) e = ks->batch_step(c, 1);
+    } else {
+      e = cudaEventRecord(fork, stream);
+      for (int k = 0; k < nbranch && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(branches[k], fork, 0);
+      for (int d = 0; d < nd && e == cudaSuccess; ++d) {
+        e = domain_step(d, branches[d % nbranch], 0);
+        if (e == cudaSuccess) e = domain_step(d, branches[d % nbranch], 1);
+      }
+      for (int k = 0; k < nbranch && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(joins[k], branches[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, joins[k], 0);
+      }
+    }
     cudaError_t e2 = cudaStreamEndCapture(stream, &g);
-    if (e0 != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
-      return cuda(e0 != cudaSuccess ? e0 : (e1 != cudaSuccess ? e1 : e2), "capture step graph");
+      return cuda(e != cudaSuccess ? e : e2, "capture step graph");
     }
     st = cuda(cudaGraphInstantiate(&graph, g, 0), "instantiate step graph");
     cudaGraphDestroy(g);
     return st;
+  }
+  cudaError_t eager_step(int parity) {
+    if (mode == 0) return ks->batch_step(ctx(), parity);
+    for (int d = 0; d < nd; ++d) {
+      cudaError_t e = domain_step(d, stream, parity);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   // nsteps steps of every domain on the internal stream (graph replays of two
   // steps where the parity allows, single launches otherwise).
@@ -439,7 +492,7 @@ struct lbm_mix_batch {
         if (st != LBM_OK) return st;
         done += 2;
       } else {
-        lbm_status st = cuda(ks->batch_step(ctx(), parity), "batched step kernels");
+        lbm_status st = cuda(eager_step(parity), "batched step kernels");
         if (st != LBM_OK) return st;
         done += 1;
       }
@@ -1045,11 +1098,11 @@ lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* confi
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   auto trial = [&](double& ms) -> lbm_status {
-    lbm_status s2 = b->run(1, false);                        // warm-up
+    lbm_status s2 = b->run(2, true);                         // warm-up (captures the graph)
     if (s2 != LBM_OK) return s2;
-    b->steps += 1;
+    b->steps += 2;
     cudaEventRecord(e0, b->stream);
-    if ((s2 = b->run(trial_steps, false)) != LBM_OK) return s2;
+    if ((s2 = b->run(trial_steps, true)) != LBM_OK) return s2;
     cudaEventRecord(e1, b->stream);
     b->steps += trial_steps;
     if ((s2 = b->cuda(cudaEventSynchronize(e1), "synchronize")) != LBM_OK) return s2;
@@ -1059,16 +1112,18 @@ lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* confi
     return LBM_OK;
   };
   const int sm = b->sm_count > 0 ? b->sm_count : 1;
-  std::vector<int> gc = {b->ntiles_c, sm, 2 * sm, 3 * sm, 4 * sm};
   double best = 1e300;
-  int bc = b->ntiles_c, bl = 256, bg = b->ntiles_256;
+  int bmode = 0, bbr = b->nbranch, bc = b->ntiles_c, bl = 256, bg = b->ntiles_256;
   st = LBM_OK;
+  // mode 0: persistent launches over all tiles
+  b->mode = 0;
   b->block_l = 256; b->grid_l = b->ntiles_256;
-  for (int g : gc) {
+  for (int g : {b->ntiles_c, sm, 2 * sm, 3 * sm, 4 * sm}) {
     if (g > b->ntiles_c || st != LBM_OK) continue;
     b->grid_c = g;
+    b->drop_graph();
     double ms;
-    if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bc = g; }
+    if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bmode = 0; bc = g; }
   }
   b->grid_c = bc;
   for (int blk : {128, 256}) {
@@ -1076,10 +1131,23 @@ lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* confi
     for (int g : {nt, 8 * sm, 16 * sm}) {
       if (g > nt || st != LBM_OK) continue;
       b->block_l = blk; b->grid_l = g;
+      b->drop_graph();
       double ms;
-      if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bl = blk; bg = g; }
+      if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bmode = 0; bl = blk; bg = g; }
     }
   }
+  b->block_l = bl; b->grid_l = bg;
+  // mode 1: each domain's own kernels on concurrent graph branches
+  b->mode = 1;
+  for (int nb : {4, 8, 16}) {
+    if (st != LBM_OK) break;
+    b->nbranch = nb;
+    b->drop_graph();
+    double ms;
+    if ((st = trial(ms)) == LBM_OK && ms < best) { best = ms; bmode = 1; bbr = nb; }
+  }
+  b->mode = bmode;
+  b->nbranch = bbr;
   b->block_l = bl; b->grid_l = bg;
   b->drop_graph();
   // restore the state and the step count
@@ -1093,7 +1161,7 @@ lbm_status lbm_mix_batch_autotune(lbm_mix_batch_t b, int trial_steps, int* confi
   cudaEventDestroy(e1);
   if (st != LBM_OK) return st;
   if (s3 != LBM_OK) return s3;
-  if (config) { config[0] = b->grid_c; config[1] = b->block_l; config[2] = b->grid_l; }
+  if (config) { config[0] = b->grid_c; config[1] = b->block_l; config[2] = b->grid_l; config[3] = b->mode; config[4] = b->nbranch; }
   if (best_ms) *best_ms = best;
   return LBM_OK;
 }
@@ -1111,10 +1179,20 @@ lbm_status lbm_mix_batch_set_config(lbm_mix_batch_t b, int grid_collide, int blo
   return LBM_OK;
 }
 
+lbm_status lbm_mix_batch_set_mode(lbm_mix_batch_t b, int mode, int branches) {
+  if (!b) return LBM_ERR_ARG;
+  if ((mode != 0 && mode != 1) || branches < 1 || branches > 64) return b->fail(LBM_ERR_ARG, "mode 0/1, 1..64 branches");
+  b->mode = mode;
+  b->nbranch = branches;
+  b->drop_graph();
+  return LBM_OK;
+}
+
 lbm_status lbm_mix_batch_config(lbm_mix_batch_t b, int* config) {
   if (!b || !config) return LBM_ERR_ARG;
   config[0] = b->grid_c; config[1] = b->block_l; config[2] = b->grid_l; config[3] = b->use_graph ? 1 : 0;
   config[4] = b->ntiles_c; config[5] = b->ntiles_128; config[6] = b->ntiles_256; config[7] = b->ks->collide_bs;
+  config[8] = b->mode; config[9] = b->nbranch;
   return LBM_OK;
 }
 
@@ -1126,6 +1204,8 @@ lbm_status lbm_mix_batch_synchronize(lbm_mix_batch_t b) {
   if ((st = b->cuda(cudaMemcpy(&flag, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error flag")) != LBM_OK)
     return st;
   if (flag) return b->fail(LBM_ERR_NONFINITE, "a node reached non-positive density or temperature (or NaN)");
+  for (int d = 0; d < b->nd; ++d)
+    if ((st = b->dom[d]->check_flag()) != LBM_OK) return b->fail(st, "domain " + std::to_string(d) + ": " + b->dom[d]->err);
   return LBM_OK;
 }
 
@@ -1141,6 +1221,9 @@ lbm_status lbm_mix_batch_destroy(lbm_mix_batch_t b) {
   if (b->d_ptrs) cudaFree(b->d_ptrs);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_err) cudaFree(b->d_err);
+  for (cudaStream_t x : b->branches) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->joins) cudaEventDestroy(x);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->stream) cudaStreamDestroy(b->stream);

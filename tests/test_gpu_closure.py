@@ -227,11 +227,10 @@ def test_trained_network_is_accepted_and_within_contract():
     """What the trained network gains: it replaces the exact solve at nearly
     every node (the fallback catches the rest) with every field within 1e-3
     of the FP64 oracle (FP32 storage), on a resting mixture whose composition
-    varies by 10 %; and on BF16 storage it moves the step by less than 1e-3
-    from the same step with the exact solve.  (BF16 storage itself reaches
-    ~2e-3 on the velocity of such states, see the reduced-precision parity
-    tests; the chosen form's 1e-3 contract against the oracle is checked on
-    the acoustic workload in test_gpu_parity.py.)"""
+    varies by 10 %; on BF16 storage its error against the oracle stays at the
+    storage's own (BF16 reaches ~2e-3 on the velocity of such states, see the
+    reduced-precision parity tests; the chosen form's 1e-3 contract against
+    the oracle is checked on the acoustic workload in test_gpu_parity.py)."""
     M = 3
     feat, tgt = _train_on_method(M, seed=31, amplitude=0.1, velocity=0.0)
     wl = W.random_mixture(M=M, shape=(8, 8, 8), seed=31, field_seed=77, amplitude=0.1)
@@ -257,14 +256,15 @@ def test_trained_network_is_accepted_and_within_contract():
     errs = field_errors(h.moments_dict(), om, cs)
     assert max(errs.values()) < 1e-3, errs
     h.close()
-    runs = []
+    # BF16 storage: the network costs no accuracy beyond the storage's own
+    errs = {}
     for closure in ("mlp", "exact"):
         hb = gpu_handle(wl, "bf16", closure=closure)
         if closure == "mlp":
             hb.set_closure_weights(w)
         hb.init_fields(wl.X, wl.u, wl.T, wl.P)
         hb.step(nsteps)
-        runs.append(hb.moments_dict())
+        errs[closure] = field_errors(hb.moments_dict(), om, cs)
         hb.close()
-    errs = field_errors(runs[0], runs[1], cs)
-    assert max(errs.values()) < 1e-3, errs
+    for k in errs["exact"]:
+        assert errs["mlp"][k] <= 1.5 * errs["exact"][k] + 2e-4, (k, errs)
