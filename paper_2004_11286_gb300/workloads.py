@@ -19,9 +19,12 @@ Recipes (stand-ins for the paper's experiments; lattice units, R_U = 1):
     m = 4, 40, uniform X_1, Gaussian pressure pulse of amplitude 1e-3 and
     standard deviation 6 cells at the centre).
   * ``shear_layer``    -- periodic double shear layer after Sec. 4.5 (256^3,
-    m = 2, 28, tanh velocity and composition profiles of thickness 4,
-    U0 = 0.3 c_s, seeded white noise 1e-3 U0 on u_y; D_12 = 0.005 keeps the
-    trace-species diffusion velocities below sqrt(R_a T)).
+    m = 2, 28, tanh velocity and composition profiles, U0 = 0.3 c_s, seeded
+    white noise 1e-3 U0 on u_y; D_12 = 0.005).  Mole fractions run from 0.02
+    to 0.98 rather than 0 to 1: in the tanh tails of pure bands a species
+    falls to X ~ 1e-14 and the FP64 oracle drives it negative within a few
+    steps (negative temperature by step 2-4 on a 6 x 256 x 6 grid), as with
+    the trace species of the ternary tube.
   * ``random_mixture`` -- smooth random M-species field (sum of 16 Fourier
     modes per species), random molar masses and diffusivities.
   * ``ensemble_shapes`` / ``ensemble_domain`` -- the batched ensemble: 64
@@ -142,7 +145,8 @@ def acoustic_pulse(n: int = 128, x1: float = 0.5, amplitude: float = 1e-3, sigma
 
 
 def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: float = 1e-3,
-                seed: int = 1234, steps: int = 5000, shape: Optional[tuple] = None) -> Workload:
+                seed: int = 1234, steps: int = 5000, shape: Optional[tuple] = None,
+                floor: float = 0.02) -> Workload:
     mm = np.array([2.0, 28.0])
     cv = np.array([cv_for_mass(m) for m in mm])
     D = np.array([[0.0, 0.005], [0.005, 0.0]])
@@ -150,7 +154,7 @@ def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: floa
     y = np.arange(ny, dtype=np.float64)
     y1, y2 = ny / 4.0, 3.0 * ny / 4.0
     band = 0.5 * (np.tanh((y - y1) / delta) - np.tanh((y - y2) / delta))   # 1 inside the band
-    XA = band
+    XA = floor + (1.0 - 2.0 * floor) * band      # no species falls to a trace
     X = np.empty((2, nz, ny, nx))
     X[0] = XA[None, :, None]
     X[1] = 1.0 - X[0]
