@@ -18,11 +18,15 @@ namespace lbm {
 // Threads per block: the deviations of all S lattices are staged in shared
 // memory (S * 27 values per thread), kept near 110 KB per block.  With the
 // learned closure (CL = 1) a block is one 128-node tile of the network.
+#ifndef LBM_COLLIDE_BS
+#define LBM_COLLIDE_BS 128
+#endif
 template <int M, class Real, int CL = 0>
 constexpr int collide_block() {
   constexpr long long per = (long long)(M + 2) * 27 * sizeof(Real);
   if constexpr (CL) return MLP_TILE;
-  return per * 128 <= 113 * 1024 ? 128 : (per * 64 <= 113 * 1024 ? 64 : 32);
+  return per * LBM_COLLIDE_BS <= 113 * 1024 ? LBM_COLLIDE_BS
+       : (per * 64 <= 113 * 1024 ? 64 : 32);
 }
 
 // Minimum resident blocks per SM asked of the register allocator, capped by
@@ -37,7 +41,7 @@ constexpr int collide_min_blocks() {
   if constexpr (CL) return 1;
   constexpr long long bytes = (long long)(M + 2) * 27 * sizeof(Real) * collide_block<M, Real>();
   constexpr long long nb = (227LL * 1024) / bytes;
-  constexpr int fit = nb >= 4 ? 4 : (nb < 1 ? 1 : (int)nb);
+  constexpr int fit = nb >= 8 ? 8 : (nb < 1 ? 1 : (int)nb);
   return LBM_COLLIDE_MINB < fit ? LBM_COLLIDE_MINB : fit;
 }
 

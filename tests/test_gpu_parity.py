@@ -321,3 +321,23 @@ def test_step_before_state_is_rejected():
         h.step(1)
     assert e.value.status == 6
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Degenerate grids: one node (every neighbour is the node itself) and single
+# rows or columns (periodic self-neighbours along the short axes).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 7), (1, 5, 1), (3, 1, 1)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_degenerate_grids_match_oracle(shape, precision):
+    wl = W.random_mixture(M=2, shape=shape, seed=900, velocity=0.03)
+    prm = oracle_params(wl)
+    pops = _perturbed_state(wl, prm, seed=9)
+    h = gpu_handle(wl, precision)
+    h.set_populations(pops)
+    ref = pops
+    for k in range(3):
+        ref = O.step(ref, prm)
+        h.step(1)
+        assert rel(h.populations(), ref) < TOL[precision], (shape, k)
+    h.close()
