@@ -56,6 +56,25 @@ def _args():
 
 
 # ---------------------------------------------------------------------------
+# Replicas over ranks (N > 1): every rank runs its own copy of the workload
+# (the step does not shard without a halo exchange); the job's time is the
+# slowest rank's and its throughput all ranks' lattice updates over it.
+# ---------------------------------------------------------------------------
+def _max_over_ranks(x: float, world: int, device) -> float:
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    return world * nodes * steps / seconds / 1e6
+
+
+# ---------------------------------------------------------------------------
 # Oracle timing (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def _oracle_sample_worker(edge: int, steps: int, warmup: int = 1):
@@ -469,13 +488,9 @@ def main():
     h.enable_kernel_timing(False)
     h.synchronize()
     clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = _max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     N = wl.nodes
-    value = world * N * a.steps / (elapsed_ms * 1e-3) / 1e6
+    value = _job_mlups(world, N, a.steps, elapsed_ms * 1e-3)
 
     # ---- roofline of the dominant kernel ----------------------------------
     alg = _algorithmic_bytes(wl.M, a.precision)
@@ -512,15 +527,11 @@ def main():
         h.moments(outp)
         sums = h.diagnostics()
         t1 = time.perf_counter()
-        e2e_s = t1 - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = _max_over_ranks(t1 - t0, world, dev)
         assert np.isfinite(sums).all()
         h2d = (wl.M + 5) * N * 8
         d2h = h.n_outputs * N * 8 + (wl.M + 5) * 8
-        e2e = {"value": round(world * N * a.steps / e2e_s / 1e6, 2), "unit": UNIT,
+        e2e = {"value": round(_job_mlups(world, N, a.steps, e2e_s), 2), "unit": UNIT,
                "h2d_bytes_per_step": round(h2d / a.steps, 1), "d2h_bytes_per_step": round(d2h / a.steps, 1),
                "note": "init_fields from pinned host fields + step(K) + get_moments to pinned host + "
                        "diagnostics, host wall clock"}
