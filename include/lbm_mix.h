@@ -53,7 +53,7 @@ extern "C" {
 typedef enum {
   LBM_OK = 0,
   LBM_ERR_ARG = 1,          /* invalid argument (message says which) */
-  LBM_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  LBM_ERR_UNSUPPORTED = 2,  /* valid request the library does not implement */
   LBM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   LBM_ERR_NONFINITE = 4,    /* a node reached rho <= 0, T <= 0 or NaN */
   LBM_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
@@ -67,7 +67,7 @@ enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
 
 /* Problem statement as the paper poses it (Secs. 2.1, 2.3, 3.1, 3.3, 3.5). */
 typedef struct {
-  int M;                      /* number of species, 1 <= M <= 8 (builds: 1,2,3,4,8) */
+  int M;                      /* number of species: kernels exist for 1, 2, 3, 4 and 8 */
   const double* molar_mass;   /* [M] m_a > 0; R_a = R_U / m_a (Eq. Ra) */
   const double* cv_molar;     /* [M] C-bar_{a,v} / R_U > 0 (Sec. 3.1, constant) */
   const double* D;            /* [M*M] row-major, symmetric binary diffusivities
