@@ -46,8 +46,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["acoustic", "ensemble", "mixture"], default="acoustic",
                     help="acoustic: the 128^3 binary pulse (default line); ensemble: 64 uneven ternary "
-                         "domains in one batched launch (BF16); mixture: M=8 192^3 random mixture, "
-                         "FP32 against BF16 + learned closure")
+                         "domains in one batched launch (BF16); mixture: M-species (default 8) random "
+                         "mixture on an n^3 grid (default 192), FP32 against BF16 + learned closure")
+    ap.add_argument("--M", type=int, default=8, help="species of the mixture workload")
     ap.add_argument("--no-chosen-form", action="store_true",
                     help="skip the BF16-storage / learned-closure comparison on the same workload")
     ap.add_argument("--oracle-sample", nargs=2, type=int, metavar=("EDGE", "STEPS"),
@@ -342,7 +343,9 @@ def _bench_ensemble(a, dev):
 def _bench_mixture(a, dev):
     import torch
     from paper_2004_11286_gb300 import binding, workloads as W
-    wl = W.random_mixture(M=8, n=192, seed=7)
+    M = a.M
+    n = a.n if a.n != 128 or M != 8 else 192
+    wl = W.random_mixture(M=M, n=n, seed=7)
     slaved = W.slaved_species(wl)
     N = wl.nodes
     peak, src = _peaks()
@@ -359,10 +362,10 @@ def _bench_mixture(a, dev):
         tgts.append(g[idx])
     ms = _timed_steps(h.step, h.stream, a.steps)
     h.close()
-    alg32 = _algorithmic_bytes(8, "fp32")["step"]
+    alg32 = _algorithmic_bytes(M, "fp32")["step"]
     out["fp32"] = {"MLUPS": round(N * a.steps / ms / 1e3, 2), "ms_per_step": round(ms / a.steps, 4),
                    "step_frac": round(alg32 * N * a.steps / (ms * 1e-3) / 1e9 / peak, 4)}
-    alg16 = _algorithmic_bytes(8, "bf16")["step"]
+    alg16 = _algorithmic_bytes(M, "bf16")["step"]
     hb = binding.from_workload(wl, precision="bf16", slaved=slaved, device=dev)
     hb.init_fields(wl.X, wl.u, wl.T, wl.P)
     hb.step(a.warmup)
@@ -373,7 +376,7 @@ def _bench_mixture(a, dev):
     feat = torch.cat(feats).contiguous()
     tgt = torch.cat(tgts).contiguous()
     hm = binding.from_workload(wl, precision="bf16", slaved=slaved, closure="mlp", device=dev)
-    hm.set_closure_weights(W.closure_initial_weights(8, seed=1))
+    hm.set_closure_weights(W.closure_initial_weights(M, seed=1))
     t0 = time.perf_counter()
     for k, lr in ((4000, 1e-3), (2000, 2e-4)):
         loss = hm.closure_train(feat, tgt, batch=4096, steps=k, lr=lr)
@@ -392,8 +395,8 @@ def _bench_mixture(a, dev):
     line = {"metric": METRIC, "value": out["fp32"]["MLUPS"], "unit": UNIT, "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "random 8-species mixture, 192^3 periodic, smooth 16-mode composition field, "
-                                   "m_a in [2,44], D_ab log-uniform in [0.005, 0.1]"},
+            "config": {"workload": f"random {M}-species mixture, {n}^3 periodic, smooth 16-mode composition "
+                                   "field, m_a in [2,44], D_ab log-uniform in [0.005, 0.1]"},
             "chosen_form": out}
     return line
 

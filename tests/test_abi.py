@@ -87,6 +87,17 @@ def test_create_rejects_bad_arguments_without_touching_cuda(built_library, field
     assert lib.lbm_mix_last_error(None).decode()
 
 
+def test_create_rejects_grids_of_2_31_nodes(built_library):
+    # neighbour indices are 32-bit: 2^31 nodes and more are refused up front
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    p, keep = _params(nx=2048, ny=1024, nz=1024)
+    h = ct.c_void_p()
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == 1
+    assert h.value is None
+    assert b"2^31" in lib.lbm_mix_last_error(None)
+
+
 def test_closure_network_only_in_fp32_arithmetic(built_library):
     # the learned closure runs in the FP32-arithmetic precisions with M >= 2
     from paper_2004_11286_gb300 import binding
