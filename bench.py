@@ -41,7 +41,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--n", type=int, default=128, help="grid edge of the acoustic-pulse workload")
+    ap.add_argument("--n", type=int, default=None,
+                    help="grid edge (acoustic pulse: 128, mixture: 192 by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["acoustic", "ensemble", "mixture"], default="acoustic",
@@ -344,7 +345,7 @@ def _bench_mixture(a, dev):
     import torch
     from paper_2004_11286_gb300 import binding, workloads as W
     M = a.M
-    n = a.n if a.n != 128 or M != 8 else 192
+    n = a.n if a.n is not None else 192
     wl = W.random_mixture(M=M, n=n, seed=7)
     slaved = W.slaved_species(wl)
     N = wl.nodes
@@ -404,6 +405,8 @@ def _bench_mixture(a, dev):
 # ---------------------------------------------------------------------------
 def main():
     a = _args()
+    if a.n is None and a.workload == "acoustic":
+        a.n = 128
     if a.oracle_sample:
         print(json.dumps(_oracle_sample_worker(*a.oracle_sample)))
         return
