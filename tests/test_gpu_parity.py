@@ -341,3 +341,21 @@ def test_degenerate_grids_match_oracle(shape, precision):
         h.step(1)
         assert rel(h.populations(), ref) < TOL[precision], (shape, k)
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# FP32 paths: the M x M system re-solved in FP64 where its condition bound
+# exceeds fp64_cond_bound (1.0 sends every node there).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("M", [3, 8])
+def test_fp64_solve_fallback_matches_oracle(M):
+    wl = W.random_mixture(M=M, shape=(4, 5, 6), seed=950 + M, velocity=0.03)
+    prm = oracle_params(wl)
+    pops = _perturbed_state(wl, prm, seed=M)
+    ref = O.step(O.step(pops, prm), prm)
+    for bound in (1.0, 0.0):                    # every node in FP64 / the default bound
+        h = gpu_handle(wl, "fp32", fp64_cond_bound=bound)
+        h.set_populations(pops)
+        h.step(2)
+        assert rel(h.populations(), ref) < TOL["fp32"], bound
+        h.close()
