@@ -21,28 +21,37 @@ namespace lbm {
 #ifndef LBM_COLLIDE_BS
 #define LBM_COLLIDE_BS 128
 #endif
+// Tiles of the network per block: two (256 nodes, 8 warps) where the stage of
+// 256 nodes, the weight image and two activation tiles fit in shared memory.
+template <int M, class Real>
+constexpr int kMlpTiles =
+    (long long)(M + 2) * 27 * sizeof(Real) * 2 * MLP_TILE + mlp_smem<M, 2>() <= 227LL * 1024 ? 2 : 1;
 template <int M, class Real, int CL = 0>
 constexpr int collide_block() {
   constexpr long long per = (long long)(M + 2) * 27 * sizeof(Real);
-  if constexpr (CL) return MLP_TILE;
+  if constexpr (CL) return MLP_TILE * kMlpTiles<M, Real>;
   return per * LBM_COLLIDE_BS <= 113 * 1024 ? LBM_COLLIDE_BS
        : (per * 64 <= 113 * 1024 ? 64 : 32);
 }
 
 // Minimum resident blocks per SM asked of the register allocator, capped by
-// what the shared-memory tile allows.  3 (168 registers per thread for
-// 128-thread blocks) measured best on GB300 for the 128^3 M = 2 FP32
-// workload: 3570 MLUPS against 3245 (1), 3246 (2) and 2956 (4).
-#ifndef LBM_COLLIDE_MINB
-#define LBM_COLLIDE_MINB 3
-#endif
+// what the shared-memory tile allows (LBM_COLLIDE_MINB overrides).  Measured
+// on GB300: M <= 2, 3 (168 registers per thread for 128-thread blocks; the
+// 128^3 M = 2 FP32 pulse 3570 MLUPS against 3245 (1), 3246 (2), 2956 (4));
+// M >= 3, 2 (255 registers, no spills; 128^3 M = 3 mixture FP32 2552
+// against 2475 at 3).
 template <int M, class Real, int CL = 0>
 constexpr int collide_min_blocks() {
   if constexpr (CL) return 1;
+#ifdef LBM_COLLIDE_MINB
+  constexpr int want = LBM_COLLIDE_MINB;
+#else
+  constexpr int want = M <= 2 ? 3 : 2;
+#endif
   constexpr long long bytes = (long long)(M + 2) * 27 * sizeof(Real) * collide_block<M, Real>();
   constexpr long long nb = (227LL * 1024) / bytes;
   constexpr int fit = nb >= 8 ? 8 : (nb < 1 ? 1 : (int)nb);
-  return LBM_COLLIDE_MINB < fit ? LBM_COLLIDE_MINB : fit;
+  return want < fit ? want : fit;
 }
 
 // Bulk (TMA engine) row loads of the populations where the grid allows them,
@@ -73,7 +82,7 @@ constexpr size_t collide_halo_bytes() {
 }
 template <int M, class Real, int CL = 0, int LD = 0>
 constexpr size_t collide_smem() {
-  if constexpr (CL) return collide_stage_bytes<M, Real, CL>() + MlpDims<M>::SMEM;
+  if constexpr (CL) return collide_stage_bytes<M, Real, CL>() + mlp_smem<M, kMlpTiles<M, Real>>();
   if constexpr (LD) return collide_stage_bytes<M, Real, CL>() + collide_halo_bytes<M, Real>() + 8;
   return collide_stage_bytes<M, Real, CL>();
 }
@@ -134,7 +143,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     if (!active) return;
   }
   const long long n = active ? n_raw : N - 1;
-  MlpBlock<M> mlp{smem_raw + collide_stage_bytes<M, Real, CL>(), 0u, 0u};
+  MlpBlock<M, kMlpTiles<M, Real>> mlp{smem_raw + collide_stage_bytes<M, Real, CL>(), 0u, 0u};
   if constexpr (CL) mlp.begin_setup(mlp_img);
   const Nbr nb = make_nbr(p, n);
 
@@ -303,7 +312,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       float f[MlpDims<M>::F];
       sm_feature_values<M, Real>(p, th, itab, r, inv_s, f);
 #pragma unroll
-      for (int k0 = 0; k0 < MlpDims<M>::F; k0 += 8) store_row8(mlp.act(), tid, k0, MlpDims<M>::F, f + k0);
+      for (int k0 = 0; k0 < MlpDims<M>::F; k0 += 8) store_row8(mlp.act(), mlp.row(), k0, MlpDims<M>::F, f + k0);
     }
     mlp.finish_setup();
     float out[MlpDims<M>::O];

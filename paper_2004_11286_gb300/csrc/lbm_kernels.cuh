@@ -251,7 +251,7 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t mlp_forward(const LaunchCtx& c, const float* feat, float* out, long long n) {
-    constexpr int smem = MlpDims<M>::SMEM;
+    constexpr int smem = mlp_smem<M, 1>();
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(mlp_forward_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

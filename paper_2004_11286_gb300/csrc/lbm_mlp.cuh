@@ -42,7 +42,6 @@ struct MlpDims {
   static constexpr int B_FLOATS = MLP_H + MLP_H + O;            // b1 | b2 | b3, FP32
   static constexpr int IMG_BYTES = W_BYTES + B_FLOATS * 4;       // device weight image
   static constexpr int ACT_BYTES = MLP_TILE * MLP_H * 2;         // one bf16 activation tile
-  static constexpr int SMEM = IMG_BYTES + ACT_BYTES + 16;        // + mbarrier + TMEM slot
   static constexpr int NW = MLP_H * F + MLP_H + MLP_H * MLP_H + MLP_H + O * MLP_H + O;  // FP32 weights
   static_assert(IMG_BYTES % 16 == 0, "16-byte copies of the weight image");
 };
@@ -156,26 +155,44 @@ __device__ __forceinline__ void store_row8(unsigned char* tile, int r, int k0, i
 }
 
 // ---------------------------------------------------------------------------
-// Per-block state of the network: weights image, activation tile, mbarrier
-// and TMEM columns.  Shared-memory layout (from `base`, 16-byte aligned):
-//   [W1 | W2 | W3 (bf16 core-matrix images) | b1 b2 b3 (FP32)] [act tile] [mbar, TMEM slot]
+// Per-block state of the network for T tiles of 128 rows (block of 128 T
+// threads, thread t on row t % 128 of tile t / 128): weights image (shared by
+// the tiles), one activation tile, mbarrier and 128 TMEM columns per tile.
+// Shared-memory layout (from `base`, 16-byte aligned):
+//   [W1 | W2 | W3 (bf16 core-matrix images) | b1 b2 b3 (FP32)] [act x T] [mbar x T] [TMEM slot]
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int T = 1>
+constexpr int mlp_smem() {
+  return (MlpDims<M>::IMG_BYTES + T * MlpDims<M>::ACT_BYTES + 8 * T + 8 + 15) / 16 * 16;
+}
+
+template <int M, int T = 1>
 struct MlpBlock {
   using D = MlpDims<M>;
+  static_assert(T == 1 || T == 2, "one or two tiles per block");
   unsigned char* base;
   uint32_t tmem;
   uint32_t phase;
-  __device__ unsigned char* act() const { return base + D::IMG_BYTES; }
+  __device__ int tile() const { return (int)threadIdx.x / MLP_TILE; }
+  __device__ int row() const { return (int)threadIdx.x % MLP_TILE; }
+  __device__ unsigned char* act() const { return base + D::IMG_BYTES + tile() * D::ACT_BYTES; }
+  __device__ unsigned char* act_of(int k) const { return base + D::IMG_BYTES + k * D::ACT_BYTES; }
   __device__ const float* bias() const { return reinterpret_cast<const float*>(base + D::W_BYTES); }
-  __device__ uint32_t mbar() const { return smem_u32(base + D::IMG_BYTES + D::ACT_BYTES); }
-  __device__ uint32_t* slot() const { return reinterpret_cast<uint32_t*>(base + D::IMG_BYTES + D::ACT_BYTES + 8); }
+  __device__ uint32_t mbar_of(int k) const { return smem_u32(base + D::IMG_BYTES + T * D::ACT_BYTES + 8 * k); }
+  __device__ uint32_t* slot() const {
+    return reinterpret_cast<uint32_t*>(base + D::IMG_BYTES + T * D::ACT_BYTES + 8 * T);
+  }
+  // TMEM address of this thread's lane quadrant in its tile's columns.
+  __device__ uint32_t lane_addr() const {
+    return tmem + (uint32_t)(MLP_TILE * tile()) + ((uint32_t)(row() & ~31) << 16);
+  }
 
   // Every thread: start the weight-image copy (completed by finish_setup).
   __device__ void begin_setup(const unsigned char* __restrict__ img) {
     for (int o = threadIdx.x * 16; o < D::IMG_BYTES; o += blockDim.x * 16) cp_async16(base + o, img + o);
-    if (threadIdx.x < 32) tmem_alloc(smem_u32(slot()), 128);
-    if (threadIdx.x == 0) mbar_init(mbar(), 1);
+    if (threadIdx.x < 32) tmem_alloc(smem_u32(slot()), MLP_TILE * T);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < T; ++k) mbar_init(mbar_of(k), 1);
     phase = 0;
   }
   __device__ void finish_setup() {
@@ -190,26 +207,28 @@ struct MlpBlock {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32) tmem_dealloc(tmem, 128);
+    if (threadIdx.x < 32) tmem_dealloc(tmem, MLP_TILE * T);
   }
 
-  // Thread 0 issues act[128 x K] . W[N x K]^T into TMEM columns [0, N); all
-  // wait.  Every thread takes the same barriers whatever happens, and the
-  // result is block-uniform (a timed-out wait sets bit 4 of *err).
+  // The first thread of each tile issues act[128 x K] . W[N x K]^T into its
+  // tile's TMEM columns; every thread waits for its tile.  Every thread takes
+  // the same barriers whatever happens, and the result is block-uniform (a
+  // timed-out wait sets bit 4 of *err).
   __device__ bool layer(uint32_t w_saddr, int K, int N, bool run, unsigned* err) {
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     bool ok = run;
     if (run) {
-      if (threadIdx.x == 0) {
+      if (row() == 0) {
         tc_fence_after();
         const uint32_t a0 = smem_u32(act()), idesc = umma_idesc_bf16(MLP_TILE, N);
+        const uint32_t d = tmem + (uint32_t)(MLP_TILE * tile());
         for (int kk = 0; kk < K / 16; ++kk)
-          umma_bf16(tmem, umma_desc(a0 + kk * 256, K), umma_desc(w_saddr + kk * 256, K), idesc, kk > 0 ? 1u : 0u);
-        umma_commit(mbar());
+          umma_bf16(d, umma_desc(a0 + kk * 256, K), umma_desc(w_saddr + kk * 256, K), idesc, kk > 0 ? 1u : 0u);
+        umma_commit(mbar_of(tile()));
       }
-      ok = mbar_wait(mbar(), phase);
+      ok = mbar_wait(mbar_of(tile()), phase);
       phase ^= 1u;
       tc_fence_after();
     }
@@ -219,21 +238,20 @@ struct MlpBlock {
   }
   // Hidden-layer epilogue: bias + GELU of this thread's row, back into act as bf16.
   __device__ void hidden_epilogue(const float* b) {
-    const int t = threadIdx.x;
-    const uint32_t lane_addr = tmem + ((uint32_t)(t & ~31) << 16);
+    const uint32_t la = lane_addr();
 #pragma unroll 1
     for (int c = 0; c < MLP_H / 16; ++c) {
       float v[16];
-      tmem_ld16(lane_addr + c * 16, v);
+      tmem_ld16(la + c * 16, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = gelu_exact(v[i] + b[c * 16 + i]);
-      store_row8(act(), t, c * 16, MLP_H, v);
-      store_row8(act(), t, c * 16 + 8, MLP_H, v + 8);
+      store_row8(act(), row(), c * 16, MLP_H, v);
+      store_row8(act(), row(), c * 16 + 8, MLP_H, v + 8);
     }
   }
 
-  // Full network for the 128 rows already written to act (K = F layout);
-  // this thread's outputs (row threadIdx.x) in out[0, O).
+  // Full network for the rows already written to this thread's tile (K = F
+  // layout); this thread's outputs in out[0, O).
   __device__ bool forward(float (&out)[D::O], unsigned* err) {
     const uint32_t w1 = smem_u32(base), w2 = w1 + D::W1_BYTES, w3 = w2 + D::W2_BYTES;
     const float* b = bias();
@@ -242,11 +260,11 @@ struct MlpBlock {
     ok = layer(w2, MLP_H, MLP_H, ok, err);
     if (ok) hidden_epilogue(b + MLP_H);
     ok = layer(w3, MLP_H, D::O, ok, err);
-    const uint32_t lane_addr = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+    const uint32_t la = lane_addr();
 #pragma unroll
     for (int c = 0; c < D::O / 16; ++c) {
       float v[16];
-      if (ok) tmem_ld16(lane_addr + c * 16, v);
+      if (ok) tmem_ld16(la + c * 16, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) out[c * 16 + i] = ok ? v[i] + b[2 * MLP_H + c * 16 + i] : 0.0f;
     }
@@ -355,7 +373,7 @@ mlp_forward_kernel(const unsigned char* __restrict__ img, const float* __restric
                    long long n, unsigned* __restrict__ err) {
   using D = MlpDims<M>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  MlpBlock<M> mlp{smem_raw, 0u, 0u};
+  MlpBlock<M, 1> mlp{smem_raw, 0u, 0u};
   mlp.begin_setup(img);
   const long long row = (long long)blockIdx.x * MLP_TILE + threadIdx.x;
   float f[D::F];
