@@ -10,7 +10,7 @@
 namespace lbm {
 
 template <int M, class Real, class Store, int PAR>
-__global__ void __launch_bounds__(collide_block<M, Real>(), collide_min_blocks<M, Real>())
+__global__ void __launch_bounds__(collide_block<M, Real, 0, Store>(), collide_min_blocks<M, Real, 0, Store>())
 collide_batch_kernel(const DevParams<Real>* __restrict__ params, void* const* __restrict__ pops,
                      void* const* __restrict__ side, const int2* __restrict__ tiles, int ntiles,
                      unsigned* __restrict__ err) {

@@ -18,15 +18,20 @@
 namespace lbm {
 
 template <class Store, class Real, class P>
-__device__ __forceinline__ Real codec_load(const P& p, const Store* __restrict__ ptr, long long idx, int L) {
+__device__ __forceinline__ Real codec_decode(const P& p, Store raw, int L) {
   if constexpr (std::is_same<Store, __half>::value) {
-    return (Real)(__half2float(ptr[idx]) * p.inv_scale[L]);
+    return (Real)(__half2float(raw) * p.inv_scale[L]);
   } else if constexpr (std::is_same<Store, __nv_bfloat16>::value) {
-    return (Real)(__bfloat162float(ptr[idx]) * p.inv_scale[L]);
+    return (Real)(__bfloat162float(raw) * p.inv_scale[L]);
   } else {
     (void)p; (void)L;
-    return (Real)ptr[idx];
+    return (Real)raw;
   }
+}
+
+template <class Store, class Real, class P>
+__device__ __forceinline__ Real codec_load(const P& p, const Store* __restrict__ ptr, long long idx, int L) {
+  return codec_decode<Store, Real>(p, ptr[idx], L);
 }
 
 template <class Store, class Real, class P>

@@ -21,15 +21,24 @@ namespace lbm {
 #ifndef LBM_COLLIDE_BS
 #define LBM_COLLIDE_BS 128
 #endif
+// The stage holds the momentum and energy populations (with their deferred
+// terms added) in the arithmetic type and the species populations as stored:
+// 16-bit storage stages them raw and decodes on use.
+template <class Real, class Store>
+using StageSp = typename std::conditional<(sizeof(Store) < sizeof(Real)), Store, Real>::type;
+template <int M, class Real, class Store>
+constexpr long long stage_per_node() {
+  return (long long)M * 27 * sizeof(StageSp<Real, Store>) + 2LL * 27 * sizeof(Real);
+}
 // Tiles of the network per block: two (256 nodes, 8 warps) where the stage of
 // 256 nodes, the weight image and two activation tiles fit in shared memory.
-template <int M, class Real>
+template <int M, class Real, class Store = Real>
 constexpr int kMlpTiles =
-    (long long)(M + 2) * 27 * sizeof(Real) * 2 * MLP_TILE + mlp_smem<M, 2>() <= 227LL * 1024 ? 2 : 1;
-template <int M, class Real, int CL = 0>
+    stage_per_node<M, Real, Store>() * 2 * MLP_TILE + mlp_smem<M, 2>() <= 227LL * 1024 ? 2 : 1;
+template <int M, class Real, int CL = 0, class Store = Real>
 constexpr int collide_block() {
-  constexpr long long per = (long long)(M + 2) * 27 * sizeof(Real);
-  if constexpr (CL) return MLP_TILE * kMlpTiles<M, Real>;
+  constexpr long long per = stage_per_node<M, Real, Store>();
+  if constexpr (CL) return MLP_TILE * kMlpTiles<M, Real, Store>;
   return per * LBM_COLLIDE_BS <= 113 * 1024 ? LBM_COLLIDE_BS
        : (per * 64 <= 113 * 1024 ? 64 : 32);
 }
@@ -40,7 +49,7 @@ constexpr int collide_block() {
 // 128^3 M = 2 FP32 pulse 3570 MLUPS against 3245 (1), 3246 (2), 2956 (4));
 // M >= 3, 2 (255 registers, no spills; 128^3 M = 3 mixture FP32 2552
 // against 2475 at 3).
-template <int M, class Real, int CL = 0>
+template <int M, class Real, int CL = 0, class Store = Real>
 constexpr int collide_min_blocks() {
   if constexpr (CL) return 1;
 #ifdef LBM_COLLIDE_MINB
@@ -48,7 +57,7 @@ constexpr int collide_min_blocks() {
 #else
   constexpr int want = M <= 2 ? 3 : 2;
 #endif
-  constexpr long long bytes = (long long)(M + 2) * 27 * sizeof(Real) * collide_block<M, Real>();
+  constexpr long long bytes = stage_per_node<M, Real, Store>() * collide_block<M, Real, 0, Store>();
   constexpr long long nb = (227LL * 1024) / bytes;
   constexpr int fit = nb >= 8 ? 8 : (nb < 1 ? 1 : (int)nb);
   return want < fit ? want : fit;
@@ -71,20 +80,20 @@ constexpr int collide_min_blocks() {
 #define LBM_SPECIES_LOOP_MIN_M 4
 #endif
 
-template <int M, class Real, int CL = 0>
+template <int M, class Real, int CL = 0, class Store = Real>
 constexpr size_t collide_stage_bytes() {
-  return (size_t)(M + 2) * Q * collide_block<M, Real, CL>() * sizeof(Real);
+  return (size_t)(stage_per_node<M, Real, Store>() * collide_block<M, Real, CL, Store>() + 15) / 16 * 16;
 }
 // Bulk row loads (LD = 1) add one halo value per staged plane and an mbarrier.
 template <int M, class Real>
 constexpr size_t collide_halo_bytes() {
   return ((size_t)(M + 2) * Q * sizeof(Real) + 7) / 8 * 8;
 }
-template <int M, class Real, int CL = 0, int LD = 0>
+template <int M, class Real, int CL = 0, int LD = 0, class Store = Real>
 constexpr size_t collide_smem() {
-  if constexpr (CL) return collide_stage_bytes<M, Real, CL>() + mlp_smem<M, kMlpTiles<M, Real>>();
-  if constexpr (LD) return collide_stage_bytes<M, Real, CL>() + collide_halo_bytes<M, Real>() + 8;
-  return collide_stage_bytes<M, Real, CL>();
+  if constexpr (CL) return collide_stage_bytes<M, Real, CL, Store>() + mlp_smem<M, kMlpTiles<M, Real, Store>>();
+  if constexpr (LD) return collide_stage_bytes<M, Real, CL, Store>() + collide_halo_bytes<M, Real>() + 8;
+  return collide_stage_bytes<M, Real, CL, Store>();
 }
 // The network closure exists for the FP32-arithmetic paths with M >= 2.
 template <int M, class Real>
@@ -132,8 +141,13 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
                                              const unsigned char* __restrict__ mlp_img,
                                              unsigned long long* __restrict__ mlp_stats, long long n_raw,
                                              unsigned char* smem_raw) {
-  constexpr int BS = collide_block<M, Real, CL>();
-  Real* sm = reinterpret_cast<Real*>(smem_raw);     // [(M+2)*27][BS], thread-private columns
+  constexpr int BS = collide_block<M, Real, CL, Store>();
+  using SpT = StageSp<Real, Store>;
+  static_assert(!LD || std::is_same<SpT, Real>::value, "bulk loads stage the stored type");
+  // Stage, thread-private columns: species [M*27][BS] (SpT), then f, g [2*27][BS] (Real).
+  SpT* const sps = reinterpret_cast<SpT*>(smem_raw);
+  Real* const sfg = reinterpret_cast<Real*>(smem_raw + (size_t)M * Q * BS * sizeof(SpT));
+  Real* const sm = reinterpret_cast<Real*>(smem_raw);   // the whole stage when SpT == Real
   const long long N = p.N;
   const int tid = threadIdx.x;
   // With the network every thread of the block takes part in its tile; the
@@ -143,7 +157,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     if (!active) return;
   }
   const long long n = active ? n_raw : N - 1;
-  MlpBlock<M, kMlpTiles<M, Real>> mlp{smem_raw + collide_stage_bytes<M, Real, CL>(), 0u, 0u};
+  MlpBlock<M, kMlpTiles<M, Real, Store>> mlp{smem_raw + collide_stage_bytes<M, Real, CL, Store>(), 0u, 0u};
   if constexpr (CL) mlp.begin_setup(mlp_img);
   const Nbr nb = make_nbr(p, n);
 
@@ -160,17 +174,26 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   // thread.  With bulk row loads at odd parity a velocity's source row sits
   // in the stage shifted by cx; the value that falls outside the segment is
   // the plane's halo value (or wraps, when the segment is the whole row).
-  Real* const halo = sm + (M + 2) * Q * BS;
+  Real* const halo = sfg + 2 * Q * BS;
   const bool whole_row = p.nx == BS;
+  // momentum/energy planes (L = M, M + 1), and species planes when SpT == Real
+  auto plane = [&](int L, int i) -> Real* {
+    return L >= M ? sfg + ((L - M) * Q + i) * BS : reinterpret_cast<Real*>(sps) + (L * Q + i) * BS;
+  };
   auto cell = [&](int L, int i, int cx) -> Real& {
+    Real* const pl = plane(L, i);
     if constexpr (LD && PAR) {
       const int li = tid - cx;
-      if (li < 0 || li >= BS) return whole_row ? sm[(L * Q + i) * BS + (li < 0 ? BS - 1 : 0)] : halo[L * Q + i];
-      return sm[(L * Q + i) * BS + li];
+      if (li < 0 || li >= BS) return whole_row ? pl[li < 0 ? BS - 1 : 0] : halo[L * Q + i];
+      return pl[li];
     } else {
       (void)cx;
-      return sm[(L * Q + i) * BS + tid];
+      return pl[tid];
     }
+  };
+  auto species_val = [&](int a, int i, int cx) -> Real {
+    if constexpr (std::is_same<SpT, Real>::value) return cell(a, i, cx);
+    else { (void)cx; return codec_decode<Store, Real>(p, sps[(a * Q + i) * BS + tid], a); }
   };
   auto accumulate = [&](auto I_, const Real (&v)[M], Real fv, Real gv) {
     constexpr int i = decltype(I_)::value;
@@ -221,7 +244,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       constexpr int cx = cx_of(i);
       Real v[M];
 #pragma unroll
-      for (int a = 0; a < M; ++a) v[a] = cell(a, i, cx);
+      for (int a = 0; a < M; ++a) v[a] = species_val(a, i, cx);
       Real& fc = cell(M, i, cx);
       Real& gc = cell(M + 1, i, cx);
       Real fv = fc, gv = gc;
@@ -239,13 +262,14 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       Real v[M];
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        v[a] = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
-        sm[(a * Q + i) * BS + tid] = v[a];
+        const Store raw = pops[(a * Q + slot) * N + node];
+        v[a] = codec_decode<Store, Real>(p, raw, a);
+        sps[(a * Q + i) * BS + tid] = std::is_same<SpT, Real>::value ? (SpT)v[a] : (SpT)raw;
       }
       const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
-      sm[(M * Q + i) * BS + tid] = fv;
+      sfg[i * BS + tid] = fv;
       const Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
-      sm[((M + 1) * Q + i) * BS + tid] = gv;
+      sfg[(Q + i) * BS + tid] = gv;
       accumulate(I_, v, fv, gv);
     });
   }
@@ -538,7 +562,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
                      + rx * ry * pf_da<Real>(cz, th.u_sp[2], x2[2], dz[a]);
         const Real e = th.rho_a[a] * d + th.rho_a_dev[a] * (rx * ry * pf_r<Real>(cz, zr[a]));
         s_e[a] += e; s_F[a] += F;
-        const Real kv = cell(a, i, cx);
+        const Real kv = species_val(a, i, cx);
         if (active)
           codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
                                    kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
@@ -575,7 +599,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];
-      const Real kv = cell(a, 13, 0);
+      const Real kv = species_val(a, 13, 0);
       if (active)
         codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
                                  kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
@@ -587,7 +611,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 // LD = 1: bulk row loads; needs Store == Real, nx a multiple of the block
 // size and a grid whose blocks are whole row segments (checked by the host).
 template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0>
-__global__ void __launch_bounds__(collide_block<M, Real, CL>(), collide_min_blocks<M, Real, CL>())
+__global__ void __launch_bounds__(collide_block<M, Real, CL, Store>(), collide_min_blocks<M, Real, CL, Store>())
 collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
                unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
                unsigned long long* __restrict__ mlp_stats) {

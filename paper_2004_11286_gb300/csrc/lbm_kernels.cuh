@@ -180,8 +180,8 @@ struct Launch {
   }
   template <int CL, int LD>
   static void collide_launch(const LaunchCtx& c, int parity, Real* side) {
-    constexpr int BS = collide_block<M, Real, CL>();
-    constexpr size_t smem = collide_smem<M, Real, CL, LD>();
+    constexpr int BS = collide_block<M, Real, CL, Store>();
+    constexpr size_t smem = collide_smem<M, Real, CL, LD, Store>();
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -202,7 +202,7 @@ struct Launch {
   template <int CL>
   static void collide(const LaunchCtx& c, int parity, Real* side) {
     if constexpr (CL == 0 && LBM_COLLIDE_BULK && M >= LBM_COLLIDE_BULK_MIN_M && std::is_same<Real, Store>::value) {
-      if (P(c).nx % collide_block<M, Real>() == 0) {
+      if (P(c).nx % collide_block<M, Real, 0, Store>() == 0) {
         collide_launch<0, 1>(c, parity, side);
         return;
       }
@@ -226,14 +226,14 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t batch_prepare() {
-    constexpr size_t smem = collide_smem<M, Real>();
+    constexpr size_t smem = collide_smem<M, Real, 0, 0, Store>();
     cudaFuncSetAttribute(collide_batch_kernel<M, Real, Store, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(collide_batch_kernel<M, Real, Store, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaGetLastError();
   }
   static cudaError_t batch_step(const BatchCtx& b, int parity) {
-    constexpr int BS = collide_block<M, Real>();
-    constexpr size_t smem = collide_smem<M, Real>();
+    constexpr int BS = collide_block<M, Real, 0, Store>();
+    constexpr size_t smem = collide_smem<M, Real, 0, 0, Store>();
     const DevParams<Real>* prm = static_cast<const DevParams<Real>*>(b.params);
     if (parity == 0)
       collide_batch_kernel<M, Real, Store, 0><<<b.grid_c, BS, smem, b.stream>>>(prm, b.pops, b.side, b.tiles_c,
@@ -294,7 +294,7 @@ struct Launch {
     k.samples = &samples; k.mlp_forward = &mlp_forward; k.mlp_pack = &mlp_pack;
     k.batch_prepare = &batch_prepare; k.batch_step = &batch_step;
     k.launches_per_step = 3;
-    k.collide_bs = collide_block<M, Real>();
+    k.collide_bs = collide_block<M, Real, 0, Store>();
     k.mlp_F = MlpDims<M>::F; k.mlp_O = MlpDims<M>::O; k.mlp_nw = MlpDims<M>::NW;
     k.mlp_img_bytes = MlpDims<M>::IMG_BYTES;
     k.mlp_step_ok = kMlpOk<M, Real> ? 1 : 0;
