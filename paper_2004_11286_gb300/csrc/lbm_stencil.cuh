@@ -19,6 +19,28 @@
 
 namespace lbm {
 
+// Four consecutive values (16-byte aligned for FP32, 32-byte for FP64).
+template <class Real>
+__device__ __forceinline__ void load4(const Real* __restrict__ f, Real* v) {
+  if constexpr (sizeof(Real) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(f);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(f);
+    const double2 b = *reinterpret_cast<const double2*>(f + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+template <class Real>
+__device__ __forceinline__ void store4(Real* __restrict__ f, const Real* v) {
+  if constexpr (sizeof(Real) == 4) {
+    *reinterpret_cast<float4*>(f) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(f) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(f + 2) = make_double2(v[2], v[3]);
+  }
+}
+
 template <class Real, int I>
 __device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, long long N, long long sender,
                                               Real& cf, Real& cg) {
@@ -123,6 +145,144 @@ __device__ __forceinline__ void grad_X_node(const G& p, Real* __restrict__ side,
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) side[(SP_X + c) * N + n] = Real(-3) * d[c];
+}
+
+// ---------------------------------------------------------------------------
+// Row-blocked stencil passes (grids with nx a multiple of 4): one thread
+// computes four consecutive nodes of a row.  The D3Q27 weights factor per
+// axis, w_i = w(c_ix) w(c_iy) w(c_iz) with w(0) = 2/3, w(+-1) = 1/6, so the
+// isotropic gradient separates over the nine neighbour rows (c_y, c_z):
+//   d_x phi = (1/72) sum_{cy,cz} W(cy) W(cz) [phi(x+1) - phi(x-1)]
+//   d_y phi = (1/72) sum_{cz} W(cz) [s(+1, cz) - s(-1, cz)]
+//   d_z phi = (1/72) sum_{cy} W(cy) [s(cy, +1) - s(cy, -1)]
+// with W(0) = 4, W(+-1) = 1 and s = phi(x-1) + 4 phi(x) + phi(x+1) on the
+// row.  Each row is read once as six values (x0-1 .. x0+4) shared by the
+// four nodes, the middle four as one vector load.
+// ---------------------------------------------------------------------------
+// Row coordinates of the four nodes n0 .. n0+3 (x0 = n0 mod nx, a multiple of 4).
+struct Row4 {
+  unsigned x0, xm, xp;       // first x, its left neighbour, the right neighbour of x0+3 (periodic)
+  unsigned ys[3], zs[3];     // wrapped row offsets for c_y, c_z = -1, 0, +1
+  __device__ __forceinline__ unsigned row(int cy, int cz) const { return zs[cz + 1] + ys[cy + 1]; }
+};
+template <class P>
+__device__ __forceinline__ Row4 make_row4(const P& p, unsigned n0) {
+  Row4 r;
+  const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
+  r.x0 = n0 % nx;
+  const unsigned t = n0 / nx, y = t % ny, z = t / ny, pl = nx * ny;
+  r.xm = r.x0 == 0 ? nx - 1 : r.x0 - 1;
+  r.xp = r.x0 + 4 == nx ? 0 : r.x0 + 4;
+  r.ys[0] = (y == 0 ? ny - 1 : y - 1) * nx;  r.ys[1] = y * nx;  r.ys[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+  r.zs[0] = (z == 0 ? nz - 1 : z - 1) * pl;  r.zs[1] = z * pl;  r.zs[2] = (z == nz - 1 ? 0 : z + 1) * pl;
+  return r;
+}
+template <class Real>
+__device__ __forceinline__ void load_row6(const Real* __restrict__ f, const Row4& r, unsigned rb, Real (&v)[6]) {
+  v[0] = f[rb + r.xm];
+  load4<Real>(f + rb + r.x0, v + 1);
+  v[5] = f[rb + r.xp];
+}
+// Adds row (cy, cz) of field f to the a-derivative accumulators d[4] (a = 0, 1, 2).
+template <class Real, int A>
+__device__ __forceinline__ void row_derivative(const Real (&v)[6], int cy, int cz, Real (&d)[4]) {
+  const Real Wy = cy ? Real(1) : Real(4), Wz = cz ? Real(1) : Real(4);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if constexpr (A == 0) d[j] += (Wy * Wz) * (v[j + 2] - v[j]);
+    else {
+      const Real s = v[j] + Real(4) * v[j + 1] + v[j + 2];
+      if constexpr (A == 1) d[j] += (cy * Wz) * s;
+      else d[j] += (cz * Wy) * s;
+    }
+  }
+}
+
+// Pass 1 on four nodes: G_a = c_omega d_a Phi_a, K = s grad C_p, theta copied.
+template <class Real>
+__device__ __forceinline__ void grad_GK_row4(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0) {
+  const long long N = p.N;
+  const Row4 r = make_row4(p, n0);
+  Real dp[3][4], dc[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dp[a][j] = dc[a][j] = Real(0);
+#pragma unroll
+  for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy) {
+      const unsigned rb = r.row(cy, cz);
+      Real v[6];
+      load_row6<Real>(side + (SP_PHI + 0) * N, r, rb, v);
+      row_derivative<Real, 0>(v, cy, cz, dp[0]);
+      if (cy) { load_row6<Real>(side + (SP_PHI + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, dp[1]); }
+      if (cz) { load_row6<Real>(side + (SP_PHI + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, dp[2]); }
+      load_row6<Real>(side + SP_CP * N, r, rb, v);
+      row_derivative<Real, 0>(v, cy, cz, dc[0]);
+      if (cy) row_derivative<Real, 1>(v, cy, cz, dc[1]);
+      if (cz) row_derivative<Real, 2>(v, cy, cz, dc[2]);
+    }
+  const unsigned own = r.row(0, 0) + r.x0;
+  Real co[4], sv[4], th[4];
+  load4<Real>(side + SP_COM * N + own, co);
+  load4<Real>(side + SP_S * N + own, sv);
+  load4<Real>(side + SP_TH * N + own, th);
+  const Real k72 = Real(1) / Real(72);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Real g[4], k[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { g[j] = co[j] * (dp[a][j] * k72); k[j] = sv[j] * (dc[a][j] * k72); }
+    store4<Real>(side + (SP_G + a) * N + own, g);
+    store4<Real>(side + (SP_K + a) * N + own, k);
+  }
+  store4<Real>(side + SP_THR * N + own, th);
+}
+
+// Pass 2 on four nodes: X_a = -d_a G_a.
+template <class Real>
+__device__ __forceinline__ void grad_X_row4(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0) {
+  const long long N = p.N;
+  const Row4 r = make_row4(p, n0);
+  Real d[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[a][j] = Real(0);
+#pragma unroll
+  for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy) {
+      const unsigned rb = r.row(cy, cz);
+      Real v[6];
+      load_row6<Real>(side + (SP_G + 0) * N, r, rb, v);
+      row_derivative<Real, 0>(v, cy, cz, d[0]);
+      if (cy) { load_row6<Real>(side + (SP_G + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, d[1]); }
+      if (cz) { load_row6<Real>(side + (SP_G + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, d[2]); }
+    }
+  const unsigned own = r.row(0, 0) + r.x0;
+  const Real k72 = Real(-1) / Real(72);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Real x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = d[a][j] * k72;
+    store4<Real>(side + (SP_X + a) * N + own, x);
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+grad_GK_row4_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+  const long long t = gtid();
+  if (4 * t < p.N) grad_GK_row4<Real>(p, side, (unsigned)(4 * t));
+}
+template <class Real>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+grad_X_row4_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+  const long long t = gtid();
+  if (4 * t < p.N) grad_X_row4<Real>(p, side, (unsigned)(4 * t));
 }
 
 template <class Real>
