@@ -219,12 +219,12 @@ struct Launch {
       collide<0>(c, parity, side);
     }
     if (c.ev) cudaEventRecord(c.ev[1], c.stream);
-    // Row-blocked stencils (four nodes per thread) where rows split into fours.
-    const bool row4 = P(c).nx % 4 == 0;
-    if (row4) grad_GK_row4_kernel<Real><<<grid_for(c.N / 4, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
+    // Row-blocked stencils (ROWV nodes per thread) where rows split evenly.
+    const bool rows = P(c).nx % ROWV == 0;
+    if (rows) grad_GK_row_kernel<Real><<<grid_for(c.N / ROWV, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     else grad_GK_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[2], c.stream);
-    if (row4) grad_X_row4_kernel<Real><<<grid_for(c.N / 4, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
+    if (rows) grad_X_row_kernel<Real><<<grid_for(c.N / ROWV, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     else grad_X_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[3], c.stream);
     return cudaGetLastError();

@@ -41,15 +41,29 @@ __device__ __forceinline__ void store4(Real* __restrict__ f, const Real* v) {
   }
 }
 
+// Read-only gathers of the deferred terms through the non-coherent data path
+// (LBM_SIDE_LDG = 1; the collide never writes the planes it gathers from).
+#ifndef LBM_SIDE_LDG
+#define LBM_SIDE_LDG 1
+#endif
+template <class Real>
+__device__ __forceinline__ Real side_ld(const Real* p) {
+#if LBM_SIDE_LDG
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
 template <class Real, int I>
 __device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, long long N, long long sender,
                                               Real& cf, Real& cg) {
   constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
-  const Real th = side[SP_THR * N + sender];
+  const Real th = side_ld(side + SP_THR * N + sender);
   Real kc = Real(0);
-  if constexpr (cx != 0) kc += (cx > 0 ? side[(SP_K + 0) * N + sender] : -side[(SP_K + 0) * N + sender]);
-  if constexpr (cy != 0) kc += (cy > 0 ? side[(SP_K + 1) * N + sender] : -side[(SP_K + 1) * N + sender]);
-  if constexpr (cz != 0) kc += (cz > 0 ? side[(SP_K + 2) * N + sender] : -side[(SP_K + 2) * N + sender]);
+  if constexpr (cx != 0) kc += (cx > 0 ? side_ld(side + (SP_K + 0) * N + sender) : -side_ld(side + (SP_K + 0) * N + sender));
+  if constexpr (cy != 0) kc += (cy > 0 ? side_ld(side + (SP_K + 1) * N + sender) : -side_ld(side + (SP_K + 1) * N + sender));
+  if constexpr (cz != 0) kc += (cz > 0 ? side_ld(side + (SP_K + 2) * N + sender) : -side_ld(side + (SP_K + 2) * N + sender));
   const Real w0 = Real(1) - th, w1 = Real(0.5) * th;
   const Real w = (cx ? w1 : w0) * (cy ? w1 : w0) * (cz ? w1 : w0);   // Eq. (weights)
   cg = w * kc;
@@ -57,7 +71,7 @@ __device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, lon
   if constexpr (c2_of(I) == 1) {
     constexpr int a = cx ? 0 : (cy ? 1 : 2);
     constexpr int sg = cx + cy + cz;
-    cf = (sg > 0 ? Real(0.5) : Real(-0.5)) * side[(SP_X + a) * N + sender];
+    cf = (sg > 0 ? Real(0.5) : Real(-0.5)) * side_ld(side + (SP_X + a) * N + sender);
   }
 }
 
@@ -148,47 +162,82 @@ __device__ __forceinline__ void grad_X_node(const G& p, Real* __restrict__ side,
 }
 
 // ---------------------------------------------------------------------------
-// Row-blocked stencil passes (grids with nx a multiple of 4): one thread
-// computes four consecutive nodes of a row.  The D3Q27 weights factor per
+// Row-blocked stencil passes (grids with nx a multiple of ROWV): one thread
+// computes ROWV consecutive nodes of a row.  The D3Q27 weights factor per
 // axis, w_i = w(c_ix) w(c_iy) w(c_iz) with w(0) = 2/3, w(+-1) = 1/6, so the
 // isotropic gradient separates over the nine neighbour rows (c_y, c_z):
 //   d_x phi = (1/72) sum_{cy,cz} W(cy) W(cz) [phi(x+1) - phi(x-1)]
 //   d_y phi = (1/72) sum_{cz} W(cz) [s(+1, cz) - s(-1, cz)]
 //   d_z phi = (1/72) sum_{cy} W(cy) [s(cy, +1) - s(cy, -1)]
 // with W(0) = 4, W(+-1) = 1 and s = phi(x-1) + 4 phi(x) + phi(x+1) on the
-// row.  Each row is read once as six values (x0-1 .. x0+4) shared by the
-// four nodes, the middle four as one vector load.
+// row.  Each row is read once as ROWV + 2 values (x0-1 .. x0+ROWV) shared by
+// the thread's nodes: the middle ones as 16-byte vector loads, the two ends
+// as scalar loads or (SHFL) from the neighbouring lanes, which hold them as
+// their own middle values, except at warp and row edges.  Every lane of a
+// warp takes part in the shuffles; lanes past the grid compute on the last
+// nodes and store nothing.
 // ---------------------------------------------------------------------------
-// Row coordinates of the four nodes n0 .. n0+3 (x0 = n0 mod nx, a multiple of 4).
-struct Row4 {
-  unsigned x0, xm, xp;       // first x, its left neighbour, the right neighbour of x0+3 (periodic)
+#ifndef LBM_STENCIL_ROW
+#define LBM_STENCIL_ROW 4
+#endif
+constexpr int ROWV = LBM_STENCIL_ROW;
+static_assert(ROWV == 4 || ROWV == 8, "row blocking of 4 or 8 nodes");
+
+// Row coordinates of the nodes n0 .. n0+ROWV-1 (x0 = n0 mod nx, a multiple of ROWV).
+struct RowV {
+  unsigned x0, xm, xp;       // first x, its left neighbour, the right neighbour of the last node (periodic)
   unsigned ys[3], zs[3];     // wrapped row offsets for c_y, c_z = -1, 0, +1
+  bool from_left, from_right;   // the end values are held by lane - 1 / lane + 1 (same row)
   __device__ __forceinline__ unsigned row(int cy, int cz) const { return zs[cz + 1] + ys[cy + 1]; }
 };
 template <class P>
-__device__ __forceinline__ Row4 make_row4(const P& p, unsigned n0) {
-  Row4 r;
+__device__ __forceinline__ RowV make_row(const P& p, unsigned n0) {
+  RowV r;
   const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
   r.x0 = n0 % nx;
   const unsigned t = n0 / nx, y = t % ny, z = t / ny, pl = nx * ny;
   r.xm = r.x0 == 0 ? nx - 1 : r.x0 - 1;
-  r.xp = r.x0 + 4 == nx ? 0 : r.x0 + 4;
+  r.xp = r.x0 + ROWV == nx ? 0 : r.x0 + ROWV;
+  const unsigned lane = threadIdx.x & 31u;
+  r.from_left = lane > 0 && r.x0 != 0;
+  r.from_right = lane < 31 && r.x0 + ROWV != nx;
   r.ys[0] = (y == 0 ? ny - 1 : y - 1) * nx;  r.ys[1] = y * nx;  r.ys[2] = (y == ny - 1 ? 0 : y + 1) * nx;
   r.zs[0] = (z == 0 ? nz - 1 : z - 1) * pl;  r.zs[1] = z * pl;  r.zs[2] = (z == nz - 1 ? 0 : z + 1) * pl;
   return r;
 }
-template <class Real>
-__device__ __forceinline__ void load_row6(const Real* __restrict__ f, const Row4& r, unsigned rb, Real (&v)[6]) {
-  v[0] = f[rb + r.xm];
-  load4<Real>(f + rb + r.x0, v + 1);
-  v[5] = f[rb + r.xp];
+template <class Real, bool SHFL>
+__device__ __forceinline__ void load_row(const Real* __restrict__ f, const RowV& r, unsigned rb, Real (&v)[ROWV + 2]) {
+  if constexpr (SHFL) {
+#pragma unroll
+    for (int q = 0; q < ROWV; q += 4) load4<Real>(f + rb + r.x0 + q, v + 1 + q);
+    const Real left = __shfl_up_sync(0xffffffffu, v[ROWV], 1);
+    const Real right = __shfl_down_sync(0xffffffffu, v[1], 1);
+    v[0] = r.from_left ? left : f[rb + r.xm];
+    v[ROWV + 1] = r.from_right ? right : f[rb + r.xp];
+  } else {
+    v[0] = f[rb + r.xm];
+#pragma unroll
+    for (int q = 0; q < ROWV; q += 4) load4<Real>(f + rb + r.x0 + q, v + 1 + q);
+    v[ROWV + 1] = f[rb + r.xp];
+  }
 }
-// Adds row (cy, cz) of field f to the a-derivative accumulators d[4] (a = 0, 1, 2).
+// End values by shuffle in the second pass only: in the first (four fields
+// per row) the shuffles raised it from 64 to 80 registers and it ran slower,
+// also when held to 64 (measured on GB300, 128^3 acoustic pulse).  Without
+// shuffles the end loads go first: issued after the vector load the pass
+// took 58 registers and ran 9 % slower.
+#ifndef LBM_GK_SHFL
+#define LBM_GK_SHFL 0
+#endif
+#ifndef LBM_X_SHFL
+#define LBM_X_SHFL 1
+#endif
+// Adds row (cy, cz) of a field to the a-derivative accumulators d[ROWV] (a = 0, 1, 2).
 template <class Real, int A>
-__device__ __forceinline__ void row_derivative(const Real (&v)[6], int cy, int cz, Real (&d)[4]) {
+__device__ __forceinline__ void row_derivative(const Real (&v)[ROWV + 2], int cy, int cz, Real (&d)[ROWV]) {
   const Real Wy = cy ? Real(1) : Real(4), Wz = cz ? Real(1) : Real(4);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < ROWV; ++j) {
     if constexpr (A == 0) d[j] += (Wy * Wz) * (v[j + 2] - v[j]);
     else {
       const Real s = v[j] + Real(4) * v[j + 1] + v[j + 2];
@@ -198,91 +247,112 @@ __device__ __forceinline__ void row_derivative(const Real (&v)[6], int cy, int c
   }
 }
 
-// Pass 1 on four nodes: G_a = c_omega d_a Phi_a, K = s grad C_p, theta copied.
+// Pass 1 on ROWV nodes: G_a = c_omega d_a Phi_a, K = s grad C_p, theta copied.
 template <class Real>
-__device__ __forceinline__ void grad_GK_row4(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0) {
+__device__ __forceinline__ void grad_GK_row(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0,
+                                            bool store) {
   const long long N = p.N;
-  const Row4 r = make_row4(p, n0);
-  Real dp[3][4], dc[3][4];
+  const RowV r = make_row(p, n0);
+  Real dp[3][ROWV], dc[3][ROWV];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) dp[a][j] = dc[a][j] = Real(0);
+    for (int j = 0; j < ROWV; ++j) dp[a][j] = dc[a][j] = Real(0);
 #pragma unroll
   for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
     for (int cy = -1; cy <= 1; ++cy) {
       const unsigned rb = r.row(cy, cz);
-      Real v[6];
-      load_row6<Real>(side + (SP_PHI + 0) * N, r, rb, v);
+      Real v[ROWV + 2];
+      load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 0) * N, r, rb, v);
       row_derivative<Real, 0>(v, cy, cz, dp[0]);
-      if (cy) { load_row6<Real>(side + (SP_PHI + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, dp[1]); }
-      if (cz) { load_row6<Real>(side + (SP_PHI + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, dp[2]); }
-      load_row6<Real>(side + SP_CP * N, r, rb, v);
+      if (cy) { load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, dp[1]); }
+      if (cz) { load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, dp[2]); }
+      load_row<Real, LBM_GK_SHFL>(side + SP_CP * N, r, rb, v);
       row_derivative<Real, 0>(v, cy, cz, dc[0]);
       if (cy) row_derivative<Real, 1>(v, cy, cz, dc[1]);
       if (cz) row_derivative<Real, 2>(v, cy, cz, dc[2]);
     }
+  if (!store) return;
   const unsigned own = r.row(0, 0) + r.x0;
-  Real co[4], sv[4], th[4];
-  load4<Real>(side + SP_COM * N + own, co);
-  load4<Real>(side + SP_S * N + own, sv);
-  load4<Real>(side + SP_TH * N + own, th);
   const Real k72 = Real(1) / Real(72);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Real g[4], k[4];
+  for (int q = 0; q < ROWV; q += 4) {
+    Real co[4], sv[4], th[4];
+    load4<Real>(side + SP_COM * N + own + q, co);
+    load4<Real>(side + SP_S * N + own + q, sv);
+    load4<Real>(side + SP_TH * N + own + q, th);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { g[j] = co[j] * (dp[a][j] * k72); k[j] = sv[j] * (dc[a][j] * k72); }
-    store4<Real>(side + (SP_G + a) * N + own, g);
-    store4<Real>(side + (SP_K + a) * N + own, k);
+    for (int a = 0; a < 3; ++a) {
+      Real g[4], k[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { g[j] = co[j] * (dp[a][q + j] * k72); k[j] = sv[j] * (dc[a][q + j] * k72); }
+      store4<Real>(side + (SP_G + a) * N + own + q, g);
+      store4<Real>(side + (SP_K + a) * N + own + q, k);
+    }
+    store4<Real>(side + SP_THR * N + own + q, th);
   }
-  store4<Real>(side + SP_THR * N + own, th);
 }
 
-// Pass 2 on four nodes: X_a = -d_a G_a.
+// Pass 2 on ROWV nodes: X_a = -d_a G_a.
 template <class Real>
-__device__ __forceinline__ void grad_X_row4(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0) {
+__device__ __forceinline__ void grad_X_row(const DevParams<Real>& p, Real* __restrict__ side, unsigned n0,
+                                           bool store) {
   const long long N = p.N;
-  const Row4 r = make_row4(p, n0);
-  Real d[3][4];
+  const RowV r = make_row(p, n0);
+  Real d[3][ROWV];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) d[a][j] = Real(0);
+    for (int j = 0; j < ROWV; ++j) d[a][j] = Real(0);
 #pragma unroll
   for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
     for (int cy = -1; cy <= 1; ++cy) {
       const unsigned rb = r.row(cy, cz);
-      Real v[6];
-      load_row6<Real>(side + (SP_G + 0) * N, r, rb, v);
+      Real v[ROWV + 2];
+      load_row<Real, LBM_X_SHFL>(side + (SP_G + 0) * N, r, rb, v);
       row_derivative<Real, 0>(v, cy, cz, d[0]);
-      if (cy) { load_row6<Real>(side + (SP_G + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, d[1]); }
-      if (cz) { load_row6<Real>(side + (SP_G + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, d[2]); }
+      if (cy) { load_row<Real, LBM_X_SHFL>(side + (SP_G + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, d[1]); }
+      if (cz) { load_row<Real, LBM_X_SHFL>(side + (SP_G + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, d[2]); }
     }
+  if (!store) return;
   const unsigned own = r.row(0, 0) + r.x0;
   const Real k72 = Real(-1) / Real(72);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Real x[4];
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = d[a][j] * k72;
-    store4<Real>(side + (SP_X + a) * N + own, x);
-  }
+    for (int q = 0; q < ROWV; q += 4) {
+      Real x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = d[a][q + j] * k72;
+      store4<Real>(side + (SP_X + a) * N + own + q, x);
+    }
 }
 
+// LBM_GK_MINB > 0 sets a minimum of resident blocks per SM (FP32); by
+// default the compiler chooses (64 registers, four blocks of 256).
+#ifndef LBM_GK_MINB
+#define LBM_GK_MINB 0
+#endif
 template <class Real>
-__global__ void __launch_bounds__(BLOCK_LIGHT)
-grad_GK_row4_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+__global__ void
+#if LBM_GK_MINB > 0
+__launch_bounds__(BLOCK_LIGHT, sizeof(Real) == 4 ? LBM_GK_MINB : 1)
+#else
+__launch_bounds__(BLOCK_LIGHT)
+#endif
+grad_GK_row_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
   const long long t = gtid();
-  if (4 * t < p.N) grad_GK_row4<Real>(p, side, (unsigned)(4 * t));
+  const bool in = ROWV * t < p.N;
+  grad_GK_row<Real>(p, side, (unsigned)(in ? ROWV * t : p.N - ROWV), in);
 }
 template <class Real>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-grad_X_row4_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
+grad_X_row_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
   const long long t = gtid();
-  if (4 * t < p.N) grad_X_row4<Real>(p, side, (unsigned)(4 * t));
+  const bool in = ROWV * t < p.N;
+  grad_X_row<Real>(p, side, (unsigned)(in ? ROWV * t : p.N - ROWV), in);
 }
 
 template <class Real>
