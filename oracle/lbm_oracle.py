@@ -34,7 +34,16 @@ the design notes):
     rho_a);
   * at omega == omega_1 exactly, the (omega - omega_1)(g* - g) term of
     Eq. (g) is replaced by its limit (q_diff and q_corr carry a
-    1/(omega - omega_1) factor).
+    1/(omega - omega_1) factor);
+  * walls (``walls_x``: the two faces normal to x, the closed tube of
+    Sec. 4.2) reflect every lattice by halfway bounce-back: a population
+    that would leave the domain returns to its node with the opposite
+    velocity at the next time level.  The isotropic derivative reads the
+    node outside a wall as the mirror image of the node inside it: even for
+    the scalars, the y and z components and the G_alpha, odd for Phi_x (the
+    wall-normal component of a momentum-like field).  The paper leaves both
+    the derivative and the wall treatment of the three-dimensional model
+    unstated.
 """
 
 from __future__ import annotations
@@ -76,6 +85,7 @@ class Params:
     R_U: float = 1.0
     coupling: str = "strong"
     slaved: int = -1
+    walls_x: bool = False           # bounce-back walls at x = -1/2 and x = nx - 1/2
     M: int = field(init=False)
 
     def __post_init__(self):
@@ -179,28 +189,49 @@ def g_ansatz(theta, M0, m, Mt):
 # Lattice operators
 # ----------------------------------------------------------------------------
 
-def _shift(phi, c):
-    """phi(x + c) on the periodic grid; phi has shape (..., nz, ny, nx)."""
-    return np.roll(phi, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(-3, -2, -1))
+def _shift(phi, c, walls_x: bool = False, odd_x: bool = False):
+    """phi(x + c); phi has shape (..., nz, ny, nx).  Periodic in every
+    direction, or, with walls_x, mirrored across the two x walls: the node
+    outside a wall takes the value of its mirror image inside, negated for a
+    field that is odd in x."""
+    out = np.roll(phi, shift=(-int(c[2]), -int(c[1])), axis=(-3, -2))
+    if not walls_x or int(c[0]) == 0:
+        return np.roll(out, shift=-int(c[0]), axis=-1)
+    nx = phi.shape[-1]
+    src = np.arange(nx) + int(c[0])
+    outside = (src < 0) | (src >= nx)
+    src = np.clip(src, 0, nx - 1)      # mirror image of x = -1 is 0, of x = nx is nx - 1
+    out = out[..., src]
+    if odd_x:
+        out = np.where(outside, -out, out)
+    return out
 
 
-def iso_derivative(phi, alpha: int):
+def iso_derivative(phi, alpha: int, walls_x: bool = False, odd_x: bool = False):
     """Second-order isotropic lattice derivative of Sec. 4.1 (reading):
     d_alpha phi(x) = 3 sum_i w_i c_{i alpha} phi(x + c_i)."""
     acc = np.zeros_like(phi, dtype=np.float64)
     for i in range(Q):
         if C[i, alpha] != 0:
-            acc = acc + _W_ISO[i] * C[i, alpha] * _shift(phi, C[i])
+            acc = acc + _W_ISO[i] * C[i, alpha] * _shift(phi, C[i], walls_x, odd_x)
     return 3.0 * acc
 
 
-def stream(post):
+def stream(post, walls_x: bool = False):
     """Propagation along the links: the value at x in direction i moves to
-    x + c_i (left-hand sides of Eqs. SMlbm, f, g). ``post`` (S, 27, nz, ny, nx)."""
+    x + c_i (left-hand sides of Eqs. SMlbm, f, g). ``post`` (S, 27, nz, ny, nx).
+    With walls_x, the value that would cross an x wall stays at its node and
+    arrives there with the opposite velocity (halfway bounce-back)."""
     out = np.empty_like(post)
     for i in range(Q):
         out[:, i] = np.roll(post[:, i], shift=(int(C[i, 2]), int(C[i, 1]), int(C[i, 0])),
                             axis=(-3, -2, -1))
+    if walls_x:
+        for i in range(Q):
+            if C[i, 0] > 0:        # arrives at x = 0 from outside: x's own value in -c_i
+                out[:, i, :, :, 0] = post[:, OPP[i], :, :, 0]
+            elif C[i, 0] < 0:      # arrives at x = nx - 1 from outside
+                out[:, i, :, :, -1] = post[:, OPP[i], :, :, -1]
     return out
 
 
@@ -350,11 +381,12 @@ def collide(pops, prm: Params, return_aux: bool = False):
     omega, omega1 = st["omega"], st["omega1"]
 
     # --- non-local fields (Sec. 4.1 derivatives of time-t moments) ---------
+    wx = prm.walls_x
     Phi = [j[a] * (1.0 - 3.0 * R * T) - rho * u[a] ** 3 for a in range(3)]
     c_om = 1.0 / omega - 0.5
-    Gs = [c_om * iso_derivative(Phi[a], a) for a in range(3)]
-    Xc = np.stack([-iso_derivative(Gs[a], a) for a in range(3)])      # Eq. (Xalpha)
-    gradY = np.stack([np.stack([iso_derivative(st["Y"][a], b) for b in range(3)])
+    Gs = [c_om * iso_derivative(Phi[a], a, wx, odd_x=(a == 0)) for a in range(3)]
+    Xc = np.stack([-iso_derivative(Gs[a], a, wx) for a in range(3)])  # Eq. (Xalpha)
+    gradY = np.stack([np.stack([iso_derivative(st["Y"][a], b, wx) for b in range(3)])
                       for a in range(M)])                              # (M, 3, ...)
 
     # --- species, Eqs. (tauab), (tau), beta_a, (SMlbm), (fstar1) ------------
@@ -440,7 +472,7 @@ def collide(pops, prm: Params, return_aux: bool = False):
 
 def step(pops, prm: Params):
     """One time step: collide at every node, then stream (Eqs. SMlbm, fwithcorrection, g)."""
-    return stream(collide(pops, prm))
+    return stream(collide(pops, prm), prm.walls_x)
 
 
 def run(pops, prm: Params, nsteps: int):
