@@ -60,7 +60,7 @@ typedef enum {
   LBM_ERR_STATE = 6         /* call out of order (e.g. step before init) */
 } lbm_status;
 
-enum { LBM_BC_PERIODIC = 0 };
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
 enum { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_FP16_STORE = 2, LBM_PREC_BF16_STORE = 3 };
 enum { LBM_COUPLE_STRONG = 0, LBM_COUPLE_WEAK = 1 };
 enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
@@ -85,7 +85,13 @@ typedef struct {
   double omega1_fixed;        /* > 0: constant omega_1 instead of Eq. (omega1) */
   double R_U;                 /* universal gas constant in lattice units (> 0) */
   int nx, ny, nz;             /* grid, each >= 1, fewer than 2^31 nodes */
-  int bc[6];                  /* -x,+x,-y,+y,-z,+z; only LBM_BC_PERIODIC */
+  int bc[6];                  /* -x,+x,-y,+y,-z,+z: all LBM_BC_PERIODIC, or
+                                 LBM_BC_BOUNCEBACK on both x faces with y and z
+                                 periodic (the closed tube of Sec. 4.2: halfway
+                                 bounce-back of every lattice; gradients mirror
+                                 the field across the wall, odd for Phi_x).
+                                 Other combinations: LBM_ERR_UNSUPPORTED; walls
+                                 with LBM_CLOSURE_MLP or in a batch likewise. */
   int slaved_species;         /* strong coupling: slaved index, -1 -> M-1 (Sec. 3.5.2) */
   int precision;              /* LBM_PREC_* */
   int coupling;               /* LBM_COUPLE_* */

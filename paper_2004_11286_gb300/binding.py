@@ -124,8 +124,9 @@ def _dp(a: Optional[np.ndarray]):
 def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), precision: str = "fp32",
                 coupling: str = "strong", slaved: int = -1, omega_fixed: float = 0.0, omega1_fixed: float = 0.0,
                 R_U: float = 1.0, fp64_cond_bound: float = 0.0, closure: str = "exact",
-                closure_bound: float = 0.0):
-    """(lbm_mix_params, keepalive arrays) for one periodic nz x ny x nx domain."""
+                closure_bound: float = 0.0, walls_x: bool = False):
+    """(lbm_mix_params, keepalive arrays) for one nz x ny x nx domain, periodic,
+    or with bounce-back walls on both x faces (walls_x)."""
     M = int(len(molar_mass))
     nz, ny, nx = (int(v) for v in shape)
     keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in (molar_mass, cv_molar, D)]
@@ -140,7 +141,7 @@ def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), pre
     p.omega_fixed, p.omega1_fixed, p.R_U = float(omega_fixed), float(omega1_fixed), float(R_U)
     p.nx, p.ny, p.nz = nx, ny, nz
     for k in range(6):
-        p.bc[k] = 0
+        p.bc[k] = 1 if (walls_x and k < 2) else 0
     p.slaved_species = int(slaved)
     p.precision = PREC[precision]
     p.coupling = COUPLING[coupling]
@@ -151,7 +152,8 @@ def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), pre
 
 
 class LbmMix:
-    """One simulation handle: a periodic nz x ny x nx grid of M species + f + g.
+    """One simulation handle: an nz x ny x nx grid of M species + f + g,
+    periodic, or closed by bounce-back walls on both x faces (walls_x).
 
     Fields cross the boundary as float64 arrays: NumPy arrays are host
     pointers, torch CUDA tensors are device pointers.
@@ -161,7 +163,7 @@ class LbmMix:
                  precision: str = "fp32", coupling: str = "strong", slaved: int = -1,
                  omega_fixed: float = 0.0, omega1_fixed: float = 0.0, R_U: float = 1.0,
                  fp64_cond_bound: float = 0.0, closure: str = "exact", closure_bound: float = 0.0,
-                 device=None, stream=None):
+                 walls_x: bool = False, device=None, stream=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -173,7 +175,7 @@ class LbmMix:
         p, self._keep = make_params(molar_mass, cv_molar, D, mu=mu, lam=lam, shape=shape, precision=precision,
                                     coupling=coupling, slaved=slaved, omega_fixed=omega_fixed,
                                     omega1_fixed=omega1_fixed, R_U=R_U, fp64_cond_bound=fp64_cond_bound,
-                                    closure=closure, closure_bound=closure_bound)
+                                    closure=closure, closure_bound=closure_bound, walls_x=walls_x)
         self._owned = True
         self.precision = precision
         with torch.cuda.device(self.device):

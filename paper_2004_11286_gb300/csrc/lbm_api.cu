@@ -43,6 +43,7 @@ size_t side_elem_bytes(int prec) { return prec == LBM_PREC_FP64 ? 8 : 4; }
 template <class Real>
 void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   d.N = s.N; d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.M = s.M; d.slaved = s.slaved; d.weak = s.weak;
+  d.wall_x = s.wall_x;
   d.omega_is_fixed = s.omega_is_fixed; d.omega1_is_fixed = s.omega1_is_fixed;
   d.omega_fixed = (Real)s.omega_fixed; d.omega1_fixed = (Real)s.omega1_fixed;
   d.R_U = (Real)s.R_U; d.cond_bound = (Real)s.cond_bound; d.closure_bound = (Real)s.closure_bound;
@@ -524,7 +525,17 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return bad("grids must have fewer than 2^31 nodes");
   if (!(p->R_U > 0.0)) return bad("R_U must be > 0");
   for (int s = 0; s < 6; ++s)
-    if (p->bc[s] != LBM_BC_PERIODIC) { g_create_error = "only periodic boundaries are built"; return LBM_ERR_UNSUPPORTED; }
+    if (p->bc[s] != LBM_BC_PERIODIC && p->bc[s] != LBM_BC_BOUNCEBACK) return bad("unknown boundary type");
+  // Built: periodic everywhere, or bounce-back walls on both x faces with
+  // periodic y and z (the closed tube).
+  const bool walls = p->bc[0] == LBM_BC_BOUNCEBACK;
+  for (int s = 0; s < 6; ++s) {
+    const int want = (s < 2 && walls) ? LBM_BC_BOUNCEBACK : LBM_BC_PERIODIC;
+    if (p->bc[s] != want) {
+      g_create_error = "boundaries built: all periodic, or bounce-back on both x faces with y, z periodic";
+      return LBM_ERR_UNSUPPORTED;
+    }
+  }
   if (p->precision < LBM_PREC_FP64 || p->precision > LBM_PREC_BF16_STORE) return bad("unknown precision");
   if (p->coupling != LBM_COUPLE_STRONG && p->coupling != LBM_COUPLE_WEAK) return bad("unknown coupling");
   if (p->closure != LBM_CLOSURE_EXACT && p->closure != LBM_CLOSURE_MLP) return bad("unknown closure");
@@ -563,6 +574,10 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     g_create_error = "the learned closure runs only in the FP32-arithmetic precisions with M >= 2";
     return LBM_ERR_UNSUPPORTED;
   }
+  if (p->closure == LBM_CLOSURE_MLP && walls) {
+    g_create_error = "the learned closure runs on periodic grids only";
+    return LBM_ERR_UNSUPPORTED;
+  }
 
   lbm_mix* h = new (std::nothrow) lbm_mix();
   if (!h) return bad("out of host memory");
@@ -574,6 +589,7 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   lbm::DevParams<double>& d = h->p64;
   d.N = h->N; d.nx = p->nx; d.ny = p->ny; d.nz = p->nz; d.M = M; d.slaved = slaved;
   d.weak = p->coupling == LBM_COUPLE_WEAK;
+  d.wall_x = walls ? 1 : 0;
   d.omega_is_fixed = p->omega_fixed > 0.0; d.omega1_is_fixed = p->omega1_fixed > 0.0;
   d.omega_fixed = p->omega_fixed; d.omega1_fixed = p->omega1_fixed; d.R_U = p->R_U;
   d.cond_bound = p->fp64_cond_bound > 0.0 ? p->fp64_cond_bound : 1e3;
@@ -973,8 +989,11 @@ lbm_status lbm_mix_batch_create(const lbm_mix_params* params, int ndomains, void
     if (params[d].M != params[0].M || params[d].precision != params[0].precision ||
         params[d].coupling != params[0].coupling)
       return bad(LBM_ERR_ARG, "all domains must share M, precision and coupling");
-  for (int d = 0; d < ndomains; ++d)
+  for (int d = 0; d < ndomains; ++d) {
     if (params[d].closure != LBM_CLOSURE_EXACT) return bad(LBM_ERR_UNSUPPORTED, "batched domains use the exact closure");
+    for (int s = 0; s < 6; ++s)
+      if (params[d].bc[s] != LBM_BC_PERIODIC) return bad(LBM_ERR_UNSUPPORTED, "batched domains are periodic");
+  }
   lbm_mix_batch* b = new (std::nothrow) lbm_mix_batch();
   if (!b) return bad(LBM_ERR_ARG, "out of host memory");
   b->nd = ndomains; b->M = params[0].M; b->prec = params[0].precision;

@@ -135,7 +135,8 @@ __device__ __forceinline__ void issue_row_loads(const DevParams<Real>& p, const 
 
 // One node's collide + stream (thread threadIdx.x of the block; the block's
 // shared memory holds the stage and, with CL = 1, the network's tile).
-template <int M, class Real, class Store, int PAR, int CL, int LD = 0>
+// WALL: bounce-back walls normal to x (register-load path only).
+template <int M, class Real, class Store, int PAR, int CL, int LD = 0, bool WALL = false>
 __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __restrict__ pops,
                                              Real* __restrict__ side, unsigned* __restrict__ err,
                                              const unsigned char* __restrict__ mlp_img,
@@ -144,6 +145,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   constexpr int BS = collide_block<M, Real, CL, Store>();
   using SpT = StageSp<Real, Store>;
   static_assert(!LD || std::is_same<SpT, Real>::value, "bulk loads stage the stored type");
+  static_assert(!(LD && WALL), "walls use the register-load path");
   // Stage, thread-private columns: species [M*27][BS] (SpT), then f, g [2*27][BS] (Real).
   SpT* const sps = reinterpret_cast<SpT*>(smem_raw);
   Real* const sfg = reinterpret_cast<Real*>(smem_raw + (size_t)M * Q * BS * sizeof(SpT));
@@ -256,9 +258,9 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
       long long node; int slot;
-      aa_read_loc(PAR, nb, n, i, node, slot);
+      aa_read_loc<WALL>(PAR, nb, n, i, node, slot);
       Real cf = Real(0), cg = Real(0);
-      if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cf, cg);
+      if constexpr (i != 13) deferred_terms<Real, i, WALL>(side, N, nb, n, cf, cg);
       Real v[M];
 #pragma unroll
       for (int a = 0; a < M; ++a) {
@@ -400,7 +402,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       constexpr int i = decltype(I_)::value;
       if constexpr (i != 13) {
         long long node; int slot;
-        aa_write_loc(PAR, nbw, n, i, node, slot);
+        aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
         const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
         s_f += e;
         const Real fv = cell(M, i, cx_of(i));
@@ -408,7 +410,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       }
     });
     long long node; int slot;
-    aa_write_loc(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
     const Real fv = cell(M, 13, 0);
     if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
   }
@@ -476,7 +478,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       if constexpr (i != 13) {
         constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
         long long node; int slot;
-        aa_write_loc(PAR, nbw, n, i, node, slot);
+        aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
         const Real uc = dotc<Real, i>(th.u);
         const Real cc = Real(0.5) * Real(c2_of(i));
         const Real ucu = Gc * uc * uc * inv_theta;
@@ -496,7 +498,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       }
     });
     long long node; int slot;
-    aa_write_loc(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
     const Real gv = cell(M + 1, 13, 0);
     if (active)
       codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
@@ -574,7 +576,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         if (i == 13) continue;
         const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
         long long node; int slot;
-        if (PAR == 0) {
+        if (PAR == 0 || (WALL && leaves_to_wall(nbw, i))) {
           node = n; slot = Q - 1 - i;
         } else {
           const unsigned xs = cx < 0 ? nbw.xs[0] : (cx > 0 ? nbw.xs[2] : nbw.xs[1]);
@@ -589,13 +591,13 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         constexpr int i = decltype(I_)::value;
         if constexpr (i != 13) {
           long long node; int slot;
-          aa_write_loc(PAR, nbw, n, i, node, slot);
+          aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
           species_velocity(i, cx_of(i), cy_of(i), cz_of(i), node, slot);
         }
       });
     }
     long long node; int slot;
-    aa_write_loc(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];
@@ -610,13 +612,14 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 
 // LD = 1: bulk row loads; needs Store == Real, nx a multiple of the block
 // size and a grid whose blocks are whole row segments (checked by the host).
-template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0>
+// WALL = 1: bounce-back walls normal to x (with LD = 0).
+template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0, int WALL = 0>
 __global__ void __launch_bounds__(collide_block<M, Real, CL, Store>(), collide_min_blocks<M, Real, CL, Store>())
 collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
                unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
                unsigned long long* __restrict__ mlp_stats) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  collide_node<M, Real, Store, PAR, CL, LD>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
+  collide_node<M, Real, Store, PAR, CL, LD, WALL != 0>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
 }
 
 }  // namespace lbm

@@ -52,6 +52,7 @@ struct DevParams {
   int M;
   int slaved;            // strong coupling: slaved species index
   int weak;              // 1 = weak coupling (Sec. 3.5.1)
+  int wall_x;            // 1 = bounce-back walls at x = -1/2 and x = nx - 1/2 (closed tube)
   int omega_is_fixed, omega1_is_fixed;
   Real omega_fixed, omega1_fixed;
   Real R_U;
@@ -108,12 +109,15 @@ __device__ __forceinline__ Real tri(const Triplet<Real>& t, int c) {
 // ---------------------------------------------------------------------------
 struct Nbr {
   unsigned xs[3], ys[3], zs[3];  // wrapped coordinates for offsets -1, 0, +1 (y, z pre-scaled); N < 2^31
+  unsigned wall;                 // bit 0: a wall lies at -x of this node, bit 1: at +x
   __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
     return (long long)(zs[dz + 1] + ys[dy + 1] + xs[dx + 1]);
   }
 };
 
-// Periodic neighbour table of node n on the grid of p (any type with nx, ny, nz).
+// Neighbour table of node n on the grid of p (any type with nx, ny, nz,
+// wall_x): periodic, except that with walls normal to x the neighbour
+// beyond a wall is the node itself (its mirror image across the wall).
 template <class P>
 __device__ __forceinline__ Nbr make_nbr(const P& p, long long n_) {
   Nbr b;
@@ -124,7 +128,9 @@ __device__ __forceinline__ Nbr make_nbr(const P& p, long long n_) {
   const unsigned y = t % ny;
   const unsigned z = t / ny;
   const unsigned pl = nx * ny;
-  b.xs[0] = x == 0 ? nx - 1 : x - 1;  b.xs[1] = x;  b.xs[2] = x == nx - 1 ? 0 : x + 1;
+  const bool w = p.wall_x != 0;
+  b.xs[0] = x == 0 ? (w ? x : nx - 1) : x - 1;  b.xs[1] = x;  b.xs[2] = x == nx - 1 ? (w ? x : 0) : x + 1;
+  b.wall = w ? ((x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u)) : 0u;
   b.ys[0] = (y == 0 ? ny - 1 : y - 1) * nx;  b.ys[1] = y * nx;  b.ys[2] = (y == ny - 1 ? 0 : y + 1) * nx;
   b.zs[0] = (z == 0 ? nz - 1 : z - 1) * pl;  b.zs[1] = z * pl;
   b.zs[2] = (z == nz - 1 ? 0 : z + 1) * pl;
@@ -142,7 +148,19 @@ __device__ __forceinline__ Nbr opaque(const Nbr& a) {
     asm volatile("mov.u32 %0, %1;" : "=r"(b.ys[k]) : "r"(a.ys[k]));
     asm volatile("mov.u32 %0, %1;" : "=r"(b.zs[k]) : "r"(a.zs[k]));
   }
+  b.wall = a.wall;
   return b;
+}
+
+// Halfway bounce-back at the walls normal to x: direction i arrives from
+// beyond a wall (its sender x - c_i is outside), or would leave through one.
+__device__ __forceinline__ bool arrives_from_wall(const Nbr& nb, int i) {
+  const int cx = cx_of(i);
+  return (cx > 0 && (nb.wall & 1u)) || (cx < 0 && (nb.wall & 2u));
+}
+__device__ __forceinline__ bool leaves_to_wall(const Nbr& nb, int i) {
+  const int cx = cx_of(i);
+  return (cx > 0 && (nb.wall & 2u)) || (cx < 0 && (nb.wall & 1u));
 }
 
 // AA pattern.  parity 0 (even time level): logical population i of node x
@@ -150,14 +168,21 @@ __device__ __forceinline__ Nbr opaque(const Nbr& a) {
 // slot opp(i) of x.  parity 1: logical population i of x lives in slot
 // opp(i) of x - c_i; the collision writes direction i to slot i of x + c_i.
 // Each node reads and writes the same set of addresses in a step.
+// Walls (WALL, halfway bounce-back) change only the odd level: a population
+// arriving from beyond a wall is the node's own opposite one, which its
+// previous odd-level collision left in slot i of the node itself; one that
+// would leave is kept at the node, in slot opp(i), for its next even level.
+template <bool WALL>
 __device__ __forceinline__ void aa_read_loc(int parity, const Nbr& nb, long long n, int i,
                                             long long& node, int& slot) {
   if (parity == 0) { node = n; slot = i; }
+  else if (WALL && arrives_from_wall(nb, i)) { node = n; slot = i; }
   else { node = nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)); slot = opp_of(i); }
 }
+template <bool WALL>
 __device__ __forceinline__ void aa_write_loc(int parity, const Nbr& nb, long long n, int i,
                                              long long& node, int& slot) {
-  if (parity == 0) { node = n; slot = opp_of(i); }
+  if (parity == 0 || (WALL && leaves_to_wall(nb, i))) { node = n; slot = opp_of(i); }
   else { node = nb.idx(cx_of(i), cy_of(i), cz_of(i)); slot = i; }
 }
 

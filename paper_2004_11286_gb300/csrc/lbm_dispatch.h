@@ -28,6 +28,7 @@ struct LaunchCtx {
 struct BatchGeom {
   long long N;
   int nx, ny, nz;
+  int wall_x;               // always 0: the batch runs periodic domains
 };
 struct BatchCtx {
   cudaStream_t stream;

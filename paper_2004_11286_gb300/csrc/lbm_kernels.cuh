@@ -120,9 +120,9 @@ diag_partial_kernel(const DevParams<Real> p, const Store* __restrict__ pops, con
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
       long long node; int slot;
-      aa_read_loc(parity, nb, n, i, node, slot);
+      aa_read_loc<true>(parity, nb, n, i, node, slot);
       Real cf = Real(0), cg = Real(0);
-      if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cf, cg);
+      if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
 #pragma unroll
       for (int a = 0; a < M; ++a) v[a] += (double)codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
       const double fv = (double)codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + (double)cf;
@@ -178,29 +178,37 @@ struct Launch {
         *c.p64, (Store*)c.pops, c.base, X, u, T, Pr);
     return cudaGetLastError();
   }
-  template <int CL, int LD>
+  template <int CL, int LD, int WALL = 0>
   static void collide_launch(const LaunchCtx& c, int parity, Real* side) {
     constexpr int BS = collide_block<M, Real, CL, Store>();
     constexpr size_t smem = collide_smem<M, Real, CL, LD, Store>();
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 0, CL, LD, WALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1, CL, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(collide_kernel<M, Real, Store, 1, CL, LD, WALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       attr = true;
     }
     if (parity == 0)
-      collide_kernel<M, Real, Store, 0, CL, LD><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+      collide_kernel<M, Real, Store, 0, CL, LD, WALL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
           P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
     else
-      collide_kernel<M, Real, Store, 1, CL, LD><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
+      collide_kernel<M, Real, Store, 1, CL, LD, WALL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
           P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
   }
   // Bulk row loads where the blocks are whole row segments and the stage
   // holds the stored type (FP64, FP32).
   template <int CL>
   static void collide(const LaunchCtx& c, int parity, Real* side) {
+    // Walls normal to x (bounce-back): register loads, exact closure (the
+    // host refuses walls with the network closure).
+    if constexpr (CL == 0) {
+      if (P(c).wall_x) {
+        collide_launch<0, 0, 1>(c, parity, side);
+        return;
+      }
+    }
     if constexpr (CL == 0 && LBM_COLLIDE_BULK && M >= LBM_COLLIDE_BULK_MIN_M && std::is_same<Real, Store>::value) {
       if (P(c).nx % collide_block<M, Real, 0, Store>() == 0) {
         collide_launch<0, 1>(c, parity, side);

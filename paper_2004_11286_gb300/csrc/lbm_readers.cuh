@@ -71,9 +71,9 @@ get_pops_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const R
   static_for<0, Q>([&](auto I_) {
     constexpr int i = decltype(I_)::value;
     long long node; int slot;
-    aa_read_loc(parity, nb, n, i, node, slot);
+    aa_read_loc<true>(parity, nb, n, i, node, slot);
     Real cf = Real(0), cg = Real(0);
-    if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx_of(i), -cy_of(i), -cz_of(i)), cf, cg);
+    if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
     for (int L = 0; L < M + 2; ++L) {
       double v = (double)codec_load<Store, Real>(p, pops, (L * Q + slot) * N + node, L);
       if (L == M) v += (double)cf;
@@ -95,7 +95,7 @@ set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const double*
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     long long node; int slot;
-    aa_read_loc(parity, nb, n, i, node, slot);
+    aa_read_loc<true>(parity, nb, n, i, node, slot);
     for (int L = 0; L < M + 2; ++L)
       codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L, (Real)(in[(L * Q + i) * N + n] - base[L * Q + i]));
   }

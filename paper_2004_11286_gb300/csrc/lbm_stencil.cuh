@@ -75,6 +75,24 @@ __device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, lon
   }
 }
 
+// The deferred terms of the population arriving in direction I at node n.
+// With walls (WALL), one arriving from beyond a wall is the node's own
+// population of direction opp(I) reflected, so its terms are the node's own
+// for opp(I): those of I at the node, negated (w_opp(I) = w_I, c_opp(I) = -c_I).
+template <class Real, int I, bool WALL>
+__device__ __forceinline__ void deferred_terms(const Real* __restrict__ side, long long N, const Nbr& nb,
+                                               long long n, Real& cf, Real& cg) {
+  if constexpr (WALL) {
+    if (arrives_from_wall(nb, I)) {
+      incoming_corr<Real, I>(side, N, n, cf, cg);
+      cf = -cf;
+      cg = -cg;
+      return;
+    }
+  }
+  incoming_corr<Real, I>(side, N, nb.idx(-cx_of(I), -cy_of(I), -cz_of(I)), cf, cg);
+}
+
 // Zeroth/first moments of the (corrected) deviations needed by the
 // thermodynamic state (Eqs. densitya, auxua, f0momDensity, f1momMomentum,
 // g0momTotalEnergy).
@@ -91,9 +109,9 @@ __device__ __forceinline__ void load_state_moments(const DevParams<Real>& p, con
     constexpr int i = decltype(I_)::value;
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     long long node; int slot;
-    aa_read_loc(parity, nb, n, i, node, slot);
+    aa_read_loc<true>(parity, nb, n, i, node, slot);
     Real cf = Real(0), cg = Real(0);
-    if constexpr (i != 13) incoming_corr<Real, i>(side, N, nb.idx(-cx, -cy, -cz), cf, cg);
+    if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
@@ -127,7 +145,13 @@ __device__ __forceinline__ void grad_GK_node(const G& p, Real* __restrict__ side
     const long long nn = nb.idx(cx, cy, cz);
     const Real w = iso_w<Real>(i);
     const Real cp = side[SP_CP * N + nn];
-    if (cx) { d[0] += (cx * w) * side[(SP_PHI + 0) * N + nn]; dc[0] += (cx * w) * cp; }
+    // beyond a wall the mirror image of Phi_x is odd, the other fields even
+    const bool mirror = (cx < 0 && (nb.wall & 1u)) || (cx > 0 && (nb.wall & 2u));
+    if (cx) {
+      const Real phx = side[(SP_PHI + 0) * N + nn];
+      d[0] += (cx * w) * (mirror ? -phx : phx);
+      dc[0] += (cx * w) * cp;
+    }
     if (cy) { d[1] += (cy * w) * side[(SP_PHI + 1) * N + nn]; dc[1] += (cy * w) * cp; }
     if (cz) { d[2] += (cz * w) * side[(SP_PHI + 2) * N + nn]; dc[2] += (cz * w) * cp; }
   }
@@ -188,6 +212,7 @@ struct RowV {
   unsigned x0, xm, xp;       // first x, its left neighbour, the right neighbour of the last node (periodic)
   unsigned ys[3], zs[3];     // wrapped row offsets for c_y, c_z = -1, 0, +1
   bool from_left, from_right;   // the end values are held by lane - 1 / lane + 1 (same row)
+  bool wlo, whi;                // walls: the left / right end value is a mirror image
   __device__ __forceinline__ unsigned row(int cy, int cz) const { return zs[cz + 1] + ys[cy + 1]; }
 };
 template <class P>
@@ -196,8 +221,11 @@ __device__ __forceinline__ RowV make_row(const P& p, unsigned n0) {
   const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, nz = (unsigned)p.nz;
   r.x0 = n0 % nx;
   const unsigned t = n0 / nx, y = t % ny, z = t / ny, pl = nx * ny;
-  r.xm = r.x0 == 0 ? nx - 1 : r.x0 - 1;
-  r.xp = r.x0 + ROWV == nx ? 0 : r.x0 + ROWV;
+  const bool w = p.wall_x != 0;
+  r.wlo = w && r.x0 == 0;
+  r.whi = w && r.x0 + ROWV == nx;
+  r.xm = r.x0 == 0 ? (w ? 0 : nx - 1) : r.x0 - 1;
+  r.xp = r.x0 + ROWV == nx ? (w ? nx - 1 : 0) : r.x0 + ROWV;
   const unsigned lane = threadIdx.x & 31u;
   r.from_left = lane > 0 && r.x0 != 0;
   r.from_right = lane < 31 && r.x0 + ROWV != nx;
@@ -205,7 +233,8 @@ __device__ __forceinline__ RowV make_row(const P& p, unsigned n0) {
   r.zs[0] = (z == 0 ? nz - 1 : z - 1) * pl;  r.zs[1] = z * pl;  r.zs[2] = (z == nz - 1 ? 0 : z + 1) * pl;
   return r;
 }
-template <class Real, bool SHFL>
+// ODD: the field is odd under the mirror at a wall (Phi_x).
+template <class Real, bool SHFL, bool ODD = false>
 __device__ __forceinline__ void load_row(const Real* __restrict__ f, const RowV& r, unsigned rb, Real (&v)[ROWV + 2]) {
   if constexpr (SHFL) {
 #pragma unroll
@@ -219,6 +248,10 @@ __device__ __forceinline__ void load_row(const Real* __restrict__ f, const RowV&
 #pragma unroll
     for (int q = 0; q < ROWV; q += 4) load4<Real>(f + rb + r.x0 + q, v + 1 + q);
     v[ROWV + 1] = f[rb + r.xp];
+  }
+  if constexpr (ODD) {
+    if (r.wlo) v[0] = -v[0];
+    if (r.whi) v[ROWV + 1] = -v[ROWV + 1];
   }
 }
 // End values by shuffle in the second pass only: in the first (four fields
@@ -264,7 +297,7 @@ __device__ __forceinline__ void grad_GK_row(const DevParams<Real>& p, Real* __re
     for (int cy = -1; cy <= 1; ++cy) {
       const unsigned rb = r.row(cy, cz);
       Real v[ROWV + 2];
-      load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 0) * N, r, rb, v);
+      load_row<Real, LBM_GK_SHFL, true>(side + (SP_PHI + 0) * N, r, rb, v);
       row_derivative<Real, 0>(v, cy, cz, dp[0]);
       if (cy) { load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 1) * N, r, rb, v); row_derivative<Real, 1>(v, cy, cz, dp[1]); }
       if (cz) { load_row<Real, LBM_GK_SHFL>(side + (SP_PHI + 2) * N, r, rb, v); row_derivative<Real, 2>(v, cy, cz, dp[2]); }

@@ -120,6 +120,33 @@ def test_closure_sizes_match_the_oracle(built_library):
         binding.closure_sizes(5)
 
 
+@pytest.mark.parametrize("bc,status", [
+    ([1, 0, 0, 0, 0, 0], 2),      # a wall on one x face only
+    ([0, 0, 1, 1, 0, 0], 2),      # walls normal to y
+    ([1, 1, 1, 1, 0, 0], 2),
+    ([7, 7, 0, 0, 0, 0], 1),      # unknown boundary type
+])
+def test_create_rejects_unbuilt_boundaries(built_library, bc, status):
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    p, keep = _params()
+    for k in range(6):
+        p.bc[k] = bc[k]
+    h = ct.c_void_p()
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == status
+    assert h.value is None
+
+
+def test_walls_with_the_network_closure_are_refused(built_library):
+    from paper_2004_11286_gb300 import binding
+    lib = binding.load_library()
+    p, keep = _params(closure=1)
+    p.bc[0] = p.bc[1] = 1
+    h = ct.c_void_p()
+    assert lib.lbm_mix_create(ct.byref(p), None, ct.byref(h)) == 2
+    assert b"periodic" in lib.lbm_mix_last_error(None)
+
+
 def test_create_rejects_nonperiodic_and_asymmetric(built_library):
     from paper_2004_11286_gb300 import binding
     import numpy as np
