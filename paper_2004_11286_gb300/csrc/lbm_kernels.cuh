@@ -111,12 +111,17 @@ diag_partial_kernel(const DevParams<Real> p, const Store* __restrict__ pops, con
   constexpr int NV = M + 5;
   __shared__ double red[DIAG_BLOCK / 32][NV];
   const long long n = gtid();
+  // A node's 27 deviations are summed in the arithmetic type (they are the
+  // stored values, already of that precision), the nodes' sums in FP64.
   double v[NV];
 #pragma unroll
   for (int s = 0; s < NV; ++s) v[s] = 0.0;
   if (n < p.N) {
     const long long N = p.N;
     const Nbr nb = make_nbr(p, n);
+    Real w[NV];
+#pragma unroll
+    for (int s = 0; s < NV; ++s) w[s] = Real(0);
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
       long long node; int slot;
@@ -124,12 +129,16 @@ diag_partial_kernel(const DevParams<Real> p, const Store* __restrict__ pops, con
       Real cf = Real(0), cg = Real(0);
       if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
 #pragma unroll
-      for (int a = 0; a < M; ++a) v[a] += (double)codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
-      const double fv = (double)codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + (double)cf;
-      v[M] += fv;
-      v[M + 1] += cx_of(i) * fv; v[M + 2] += cy_of(i) * fv; v[M + 3] += cz_of(i) * fv;
-      v[M + 4] += (double)codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + (double)cg;
+      for (int a = 0; a < M; ++a) w[a] += codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+      const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+      w[M] += fv;
+      if constexpr (cx_of(i) != 0) w[M + 1] += cx_of(i) * fv;
+      if constexpr (cy_of(i) != 0) w[M + 2] += cy_of(i) * fv;
+      if constexpr (cz_of(i) != 0) w[M + 3] += cz_of(i) * fv;
+      w[M + 4] += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
     });
+#pragma unroll
+    for (int s = 0; s < NV; ++s) v[s] = (double)w[s];
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
