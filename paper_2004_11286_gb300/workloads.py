@@ -103,7 +103,11 @@ def _p0(X_mean, molar_mass, T):
 
 
 def ternary_tube(nx: int = 64, ny: int = 4, nz: int = 4, steps: int = 1000,
-                 width: float = 8.0) -> Workload:
+                 width: float = 8.0, closed: bool = False) -> Workload:
+    """Ternary H2/Ar/CH4 Loschmidt tube (Sec. 4.2): left half (0.5, 0.5, 0),
+    right half (0.5, 0, 0.5), tanh steps of the given width.  Periodic (two
+    steps, at the middle and across the periodic edge), or ``closed`` by walls
+    normal to x (one step at the middle)."""
     mm = np.array([2.0, 40.0, 16.0])
     cv = np.array([cv_for_mass(m) for m in mm])
     D = np.array([[0.0, 0.05, 0.05], [0.05, 0.0, 0.01], [0.05, 0.01, 0.0]])
@@ -111,9 +115,12 @@ def ternary_tube(nx: int = 64, ny: int = 4, nz: int = 4, steps: int = 1000,
     XR = np.array([0.5, 0.0, 0.5])
     x = np.arange(nx, dtype=np.float64)
     h = nx / 2.0
-    # periodic double tanh step: right state on [h, nx), left on [0, h)
-    s = 0.5 * (np.tanh((x - (h - 0.5)) / width) - np.tanh((x - (nx - 0.5)) / width)
-               - np.tanh((x + 0.5) / width) + 1.0)
+    if closed:
+        s = 0.5 * (1.0 + np.tanh((x - (h - 0.5)) / width))
+    else:
+        # periodic double tanh step: right state on [h, nx), left on [0, h)
+        s = 0.5 * (np.tanh((x - (h - 0.5)) / width) - np.tanh((x - (nx - 0.5)) / width)
+                   - np.tanh((x + 0.5) / width) + 1.0)
     X = (1.0 - s)[None] * XL[:, None] + s[None] * XR[:, None]
     X = np.broadcast_to(X[:, None, None, :], (3, nz, ny, nx)).copy()
     X = X / X.sum(axis=0, keepdims=True)

@@ -1,7 +1,9 @@
-"""Physics of the GPU step at the benchmark's full size, independent of the
-oracle: the speed of sound of the binary acoustic pulse (128^3, m = 4, 40,
+"""Physics of the GPU step, independent of the oracle: the speed of sound of
+the binary acoustic pulse at the benchmark's full size (128^3, m = 4, 40,
 FP32, 2000 steps) for mole fractions 0.2, 0.5 and 0.8 against the mixture's
-ideal-gas closed form sqrt(gamma R T) (Secs. 4.1, 4.4, Eq. soundSpeed)."""
+ideal-gas closed form sqrt(gamma R T) (Secs. 4.1, 4.4, Eq. soundSpeed); and
+the osmotic-diffusion transient of the closed ternary tube against the
+linearised Maxwell-Stefan theory (Sec. 4.2)."""
 
 import numpy as np
 import pytest
@@ -83,3 +85,40 @@ def test_acoustic_pulse_speed_of_sound(x1):
     assert abs(speeds[0] / cs - 1.0) < 1e-2, (x1, speeds, cs)
     assert speeds[0] > speeds[1] > speeds[2]        # normal dispersion: shorter waves are slower
     assert abs(c0 / c_iso - 1.0) > 0.1              # the adiabatic, not the isothermal speed
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_closed_tube_osmotic_diffusion_transient(precision):
+    """Sec. 4.2: the closed H2/Ar/CH4 tube (64 x 4 x 4, walls on both x
+    faces), 40000 steps: hydrogen, at the same mole fraction in both halves,
+    builds up a half-tube difference and loses it again (osmotic diffusion).
+    Its whole transient, and the argon and methane differences, follow the
+    linearised Maxwell-Stefan theory."""
+    from ms_theory import half_tube_differences, osmotic_tube
+    from paper_2004_11286_gb300 import binding
+    L, steps, every = 64, 40000, 4000
+    X0, D = osmotic_tube(L)
+    mm, cv = np.array([2.0, 40.0, 16.0]), np.array([2.5, 1.5, 3.0])
+    T = 0.2
+    P0 = T / float(np.dot(X0.mean(axis=1), mm))
+    mu = np.full(3, 0.1 * P0)
+    shape = (4, 4, L)
+    h = binding.LbmMix(mm, cv, D, mu=mu, lam=mu * (cv + 1.0) / mm / 0.71, shape=shape, precision=precision,
+                       slaved=1, walls_x=True)
+    X = np.broadcast_to(X0[:, None, None, :], (3,) + shape).copy()
+    h.init_fields(X, np.zeros((3,) + shape), np.full(shape, T), np.full(shape, P0))
+    times, sim = [], []
+    for t in range(every, steps + 1, every):
+        h.step(every)
+        Xs = h.moments_dict()["X"].mean(axis=(1, 2))
+        sim.append(Xs[:, :L // 2].mean(axis=1) - Xs[:, L // 2:].mean(axis=1))
+        times.append(t)
+    h.close()
+    sim = np.array(sim)
+    th = half_tube_differences(X0, D, times)
+    peak = float(th[:, 0].max())
+    k = int(np.argmax(sim[:, 0]))
+    assert 0 < k < len(times) - 1                                    # rises, then falls
+    assert np.abs(sim[:, 0] - th[:, 0]).max() < 0.03 * peak, (sim[:, 0], th[:, 0])
+    d0 = X0[1, :L // 2].mean() - X0[1, L // 2:].mean()
+    assert np.abs(sim[:, 1:] - th[:, 1:]).max() < 0.01 * d0, (sim[:, 1:], th[:, 1:])
