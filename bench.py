@@ -188,12 +188,15 @@ def _peaks():
 
 
 def _kernel_source_hash():
+    """Hash of the kernel sources and the compiler flags they are built with."""
+    from paper_2004_11286_gb300 import build
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2004_11286_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
+    h.update(" ".join(build.NVCC_FLAGS).encode())
     return h.hexdigest()[:16]
 
 
