@@ -4,6 +4,8 @@ on small periodic grids (no GPU).
 * Sec. 4.1 / 4.4, Eq. (soundSpeed): the speed of sound is sqrt(gamma R T) of
   the mixture (not the isothermal sqrt(R T)); binary and ternary compositions,
   including S1 of Eq. (soundTestConditions).
+* Sec. 3.3, Eqs. (lambda), (omega1): an isobaric temperature wave decays at
+  lambda k^2 / (rho C_p).
 * Sec. 3.3, Eq. (mu): a shear wave decays at nu k^2, nu = (1/omega - 1/2) R T,
   also in a frame moving along the wave vector (Galilean invariance, which the
   D3Q27 correction of Eq. fwithcorrection maintains).
@@ -178,3 +180,36 @@ def test_closed_tube_osmotic_diffusion_against_maxwell_stefan_theory():
     assert np.abs(sim[:, 0] - th[:, 0]).max() < 0.03 * peak, (sim[:, 0], th[:, 0])
     d0 = X0[1, :L // 2].mean() - X0[1, L // 2:].mean()
     assert np.abs(sim[:, 1:] - th[:, 1:]).max() < 0.01 * d0
+
+
+@pytest.mark.parametrize("omega1", [1.2, 1.6])
+def test_thermal_wave_conductivity(omega1):
+    """Sec. 3.3, Eqs. (lambda), (omega1), (conductivityMixture): a small
+    isobaric temperature wave (the entropy mode) decays at lambda k^2 /
+    (rho C_p).  Every species gets the same lambda_a, so the Mathur mixture
+    conductivity is lambda_a itself; He/Ar are monatomic, so C_p = (5/2) R.
+    lambda is chosen for omega_1 = 1.2 and 1.6 (the hydrodynamic regime); the
+    lattice adds an O(k^2) excess: measured 1.2 % at 24 cells (2.5 % at 16)."""
+    mm, cv, X0, T0 = [4.0, 40.0], [1.5, 1.5], [0.5, 0.5], 0.2
+    M = 2
+    mbar = float(np.dot(X0, mm))
+    P0 = T0 / mbar
+    Cp = 2.5 / mbar
+    lam0 = (1.0 / omega1 - 0.5) * P0 * Cp
+    prm = O.Params(np.array(mm), np.array(cv), np.array([[0.0, 0.05], [0.05, 0.0]]), mu=np.full(M, 0.1 * P0),
+                   lam=np.full(M, lam0), slaved=1)
+    n, steps = 24, 1200
+    k = 2 * np.pi / n
+    shape = (1, 1, n)
+    x = np.arange(n)
+    X = np.stack([np.full(shape, v) for v in X0])
+    T = T0 * (1.0 + 1e-3 * np.cos(k * x))[None, None, :]
+    pops = O.init_populations(X, np.zeros((3,) + shape), T, np.full(shape, P0), prm)
+    amp = []
+    for _ in range(steps):
+        amp.append(np.abs(np.fft.rfft(O.macroscopic(pops, prm)["T"][0, 0])[1]))
+        pops = O.step(pops, prm)
+    rate = -np.log(amp[-1] / amp[300]) / (steps - 1 - 300)
+    rho0 = P0 * mbar / T0
+    alpha = lam0 / (rho0 * Cp)
+    assert abs(rate / (alpha * k * k) - 1.0) < 2e-2, rate / (alpha * k * k)
