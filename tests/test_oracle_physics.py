@@ -1,5 +1,5 @@
 """Physical pins of the oracle: hydrodynamic limits the paper derives, checked
-on small periodic grids (no GPU).
+on small grids, periodic or closed by walls (no GPU).
 
 * Sec. 4.1 / 4.4, Eq. (soundSpeed): the speed of sound is sqrt(gamma R T) of
   the mixture (not the isothermal sqrt(R T)); binary and ternary compositions,
