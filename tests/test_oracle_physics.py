@@ -4,8 +4,14 @@ on small grids, periodic or closed by walls (no GPU).
 * Sec. 4.1 / 4.4, Eq. (soundSpeed): the speed of sound is sqrt(gamma R T) of
   the mixture (not the isothermal sqrt(R T)); binary and ternary compositions,
   including S1 of Eq. (soundTestConditions).
-* Sec. 3.3, Eqs. (lambda), (omega1): an isobaric temperature wave decays at
-  lambda k^2 / (rho C_p).
+* Sec. 3.3, Eqs. (lambda), (omega1), (conductivityMixture): an isobaric
+  temperature wave decays at lambda k^2 / (rho C_p), with equal species
+  conductivities and with unequal ones (Mathur's rule).
+* Sec. 3.2 Eqs. (interdiffusion), (corrFourier); Sec. 3.3 Eq. (qneq): isobaric,
+  isothermal interdiffusion of two ideal gases with unequal specific heats
+  per mass leaves the temperature uniform: the enthalpy the diffusion fluxes
+  carry (the second term of Eq. qneq) exactly balances the change of the
+  internal energy, and the Fourier term sees no spurious grad Y_a part.
 * Sec. 3.3, Eq. (mu): a shear wave decays at nu k^2, nu = (1/omega - 1/2) R T,
   also in a frame moving along the wave vector (Galilean invariance, which the
   D3Q27 correction of Eq. fwithcorrection maintains).
@@ -182,22 +188,26 @@ def test_closed_tube_osmotic_diffusion_against_maxwell_stefan_theory():
     assert np.abs(sim[:, 1:] - th[:, 1:]).max() < 0.01 * d0
 
 
-@pytest.mark.parametrize("omega1", [1.2, 1.6])
-def test_thermal_wave_conductivity(omega1):
+@pytest.mark.parametrize("omega1,ratio", [(1.2, 1.0), (1.6, 1.0), (1.2, 4.0), (1.6, 4.0)])
+def test_thermal_wave_conductivity(omega1, ratio):
     """Sec. 3.3, Eqs. (lambda), (omega1), (conductivityMixture): a small
     isobaric temperature wave (the entropy mode) decays at lambda k^2 /
-    (rho C_p).  Every species gets the same lambda_a, so the Mathur mixture
-    conductivity is lambda_a itself; He/Ar are monatomic, so C_p = (5/2) R.
-    lambda is chosen for omega_1 = 1.2 and 1.6 (the hydrodynamic regime); the
-    lattice adds an O(k^2) excess: measured 1.2 % at 24 cells (2.5 % at 16)."""
+    (rho C_p).  He/Ar are monatomic, so C_p = (5/2) R.  lambda is chosen for
+    omega_1 = 1.2 and 1.6 (the hydrodynamic regime).  With ratio = 1 every
+    species has the same lambda_a, which is then the mixture value; with
+    ratio = 4, lambda_1 = 4 lambda_2 and at X = (1/2, 1/2) Mathur's rule gives
+    lambda = (2.5 + 1.6) lambda_2 / 2 = 2.05 lambda_2, where the arithmetic
+    mean alone would be 2.5 lambda_2 (22 % faster decay).  The lattice adds
+    an O(k^2) excess: measured 1.2 % at 24 cells (2.5 % at 16)."""
     mm, cv, X0, T0 = [4.0, 40.0], [1.5, 1.5], [0.5, 0.5], 0.2
     M = 2
     mbar = float(np.dot(X0, mm))
     P0 = T0 / mbar
     Cp = 2.5 / mbar
     lam0 = (1.0 / omega1 - 0.5) * P0 * Cp
+    lam2 = lam0 / (0.5 * (0.5 * (ratio + 1.0) + 1.0 / (0.5 * (1.0 / ratio + 1.0))))
     prm = O.Params(np.array(mm), np.array(cv), np.array([[0.0, 0.05], [0.05, 0.0]]), mu=np.full(M, 0.1 * P0),
-                   lam=np.full(M, lam0), slaved=1)
+                   lam=np.array([ratio * lam2, lam2]), slaved=1)
     n, steps = 24, 1200
     k = 2 * np.pi / n
     shape = (1, 1, n)
@@ -213,3 +223,68 @@ def test_thermal_wave_conductivity(omega1):
     rho0 = P0 * mbar / T0
     alpha = lam0 / (rho0 * Cp)
     assert abs(rate / (alpha * k * k) - 1.0) < 2e-2, rate / (alpha * k * k)
+
+
+def _interdiffusion_run(n, steps, amp=0.05, rho0=2.0):
+    """Isobaric, isothermal binary interdiffusion of monatomic He/Ar-like
+    species (m = 4, 40: per-mass C_p differs tenfold): a mole-fraction wave
+    of amplitude ``amp`` at uniform T0 and P0, zero velocity, mean density
+    ``rho0`` (not 1, so a dropped rho factor shows).  Returns the largest
+    deviation over the run of the temperature with its adiabatic part
+    removed, T (P / P0)^(-(gamma - 1)/gamma) / T0 - 1 (gamma = 5/3 for any
+    composition of monatomic gases), and the decay of the X_1 mode.
+
+    The start-up launches a weak sound wave (the density changes with the
+    composition while u = 0); its temperature swing is adiabatic and is what
+    the correction removes."""
+    mm, cv, X1, T0 = np.array([4.0, 40.0]), np.array([1.5, 1.5]), 0.5, 0.2
+    mbar = X1 * mm[0] + (1 - X1) * mm[1]
+    P0 = rho0 * T0 / mbar
+    mu = np.full(2, 0.1 * P0)
+    prm = O.Params(mm, cv, np.array([[0.0, 0.05], [0.05, 0.0]]), mu=mu, lam=mu * (cv + 1.0) / mm / 0.71,
+                   slaved=1)
+    shape = (1, 1, n)
+    k = 2 * np.pi / n
+    X = np.empty((2,) + shape)
+    X[0] = X1 + amp * np.cos(k * np.arange(n))
+    X[1] = 1 - X[0]
+    pops = O.init_populations(X, np.zeros((3,) + shape), np.full(shape, T0), np.full(shape, P0), prm)
+    dev = 0.0
+    for _ in range(steps):
+        pops = O.step(pops, prm)
+        mac = O.macroscopic(pops, prm)
+        Ts = mac["T"] * (mac["P"] / P0) ** -0.4
+        dev = max(dev, float(np.abs(Ts / T0 - 1.0).max()))
+    Xm = abs(np.fft.rfft(mac["X"][0, 0, 0])[1]) * 2 / n
+    return dev, Xm / amp
+
+
+def test_isobaric_interdiffusion_keeps_temperature_uniform():
+    """Sec. 3.2, Eqs. (interdiffusion), (corrFourier), (gstareq1mom); Sec. 3.3,
+    Eq. (qneq).  For ideal gases at uniform T and P, the internal-energy
+    change of interdiffusion, T sum_a C_{a,v} d_t rho_a, is balanced exactly
+    by the divergence of sum_a rho_a H_a u_a (enthalpy carried by the species
+    velocities, the interdiffusion term of Eq. qneq with P u), since the
+    molar-averaged velocity has no divergence; so T stays uniform and any
+    error in the enthalpy flux shows as a temperature wave.  The Fourier term
+    of Eq. (qneq) must see grad T only: without q^corr the lumped enthalpy
+    gradient adds a flux proportional to T grad C_p.
+
+    Measured: 7.9e-5 at 32 cells, an O(k^2) lattice residual (2.2e-5 at 64
+    cells).  Mutations of the oracle, each run once and then reverted,
+    give (same measure, 32 cells): q^diff dropped 3.6e-2, sign flipped 7.1e-2,
+    without rho 1.7e-2, omega instead of omega_1 in its prefactor 1.1e-2, X_a
+    instead of Y_a 2.4e-1; q^corr dropped 2.2e-3, sign flipped 4.2e-3, its
+    1/2 dropped 2.0e-3, without P 1.2e-1; H_a = C_{a,v} T 1.4e-2."""
+    dev, decay = _interdiffusion_run(32, 300)
+    assert dev < 3e-4, dev
+    assert decay < 0.7                    # the composition has actually moved
+
+
+@pytest.mark.slow
+def test_isobaric_interdiffusion_residual_is_second_order():
+    """The residual of the test above is a lattice error of O(k^2): doubling
+    the wavelength (and the diffusion time, x4) divides it by about 4."""
+    d32, _ = _interdiffusion_run(32, 300)
+    d64, _ = _interdiffusion_run(64, 1200)
+    assert d64 < d32 / 2.5, (d32, d64)

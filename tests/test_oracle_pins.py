@@ -304,6 +304,35 @@ def test_wilke_binary_textbook_value():
     assert np.isclose((1 / st["omega"].item() - 0.5) * P, mu_mix, rtol=1e-12)
 
 
+def test_mathur_binary_hand_value():
+    """Eq. (conductivityMixture) with unequal species conductivities, worked
+    by hand for X = (1/4, 3/4), lambda = (0.02, 0.004):
+      sum X_a lambda_a = 0.005 + 0.003 = 0.008,
+      sum X_a / lambda_a = 12.5 + 187.5 = 200,
+      lambda = (0.008 + 1/200) / 2 = 0.0065,
+    then Eq. (omega1).  The arithmetic mean alone (0.008), the harmonic one
+    alone (0.005) or a missing 1/2 (0.013) all give another omega_1.  C_p is
+    written out from Mayer's relation: (cv + 1) R_U / m_a per species, mixed
+    by mass fraction."""
+    m = np.array([4.0, 40.0])
+    cv = np.array([1.5, 2.5])
+    prm = O.Params(m, cv, np.array([[0, .05], [.05, 0]]), mu=np.array([1e-3, 1e-3]),
+                   lam=np.array([0.02, 0.004]))
+    X = np.array([0.25, 0.75]).reshape(2, 1, 1, 1)
+    T, P = 0.3, 0.04
+    pops = O.init_populations(X, np.zeros((3, 1, 1, 1)), np.full((1, 1, 1), T), np.full((1, 1, 1), P), prm)
+    st = O.node_state(O.moments(pops, prm), prm)
+    mbar = 0.25 * 4.0 + 0.75 * 40.0                       # 31
+    Y = np.array([0.25 * 4.0, 0.75 * 40.0]) / mbar
+    Cp = Y[0] * 2.5 / 4.0 + Y[1] * 3.5 / 40.0
+    lam = 0.0065
+    assert np.isclose(st["P"].item(), P, rtol=1e-13)
+    assert np.isclose(st["Cp"].item(), Cp, rtol=1e-13)
+    assert np.isclose(st["omega1"].item(), 2 * P * Cp / (P * Cp + 2 * lam), rtol=1e-12)
+    # Eq. (lambda) read back: lambda = (1/omega_1 - 1/2) P C_p
+    assert np.isclose((1 / st["omega1"].item() - 0.5) * P * Cp, lam, rtol=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # Special case: identical species reduce to the single-component compressible
 # model (Sec. 5, last paragraph): f and g do not depend on how the mass is split.
