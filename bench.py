@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the fused multicomponent D3Q27 stream-and-collide step.
 
-Workload (N = 1 GPU): the binary acoustic pulse on a 128^3 periodic grid,
-M = 2 species (molar masses 4, 40), FP32, i.e. 2 species + f + g lattices,
-108 populations per node.  One bench step = one lattice time step of the
-whole grid (all lattices).  The populations (906 MB) are larger than L2, so
-no flush is needed between steps.
+Workload (N = 1 GPU, the default line): the two-component Kelvin-Helmholtz
+shear layer on a 256^3 periodic grid, M = 2 species (molar masses 2, 28),
+plain FP32, i.e. 2 species + f + g lattices, 108 populations per node; the
+chosen form (BF16-stored populations, then BF16 plus the learned
+Stefan-Maxwell closure) on the same workload; per-field errors against the
+FP64 oracle on a reduced copy of the workload; secondary lines for the
+eight-species 192^3 mixture (FP32, BF16, BF16 + closure) and the 64-domain
+ensemble.  One bench step = one lattice time step of the whole grid (all
+lattices).  The populations (7.2 GB) are larger than L2, so no flush is
+needed between steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
 (the only other implementation of the method) on a bounded periodic sample of
 the same workload on the host cores.  Under torchrun each rank runs an
-independent replica (the single-GPU problem does not shard without a halo
-exchange, which is not built): value = all ranks' lattice updates / max time.
+independent replica (value = all ranks' lattice updates / max time).
 """
 
 from __future__ import annotations
@@ -37,22 +41,26 @@ FALLBACK_HBM_GBS = 6800.0
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--n", type=int, default=None,
-                    help="grid edge (acoustic pulse: 128, mixture: 192 by default)")
+                    help="grid edge (shear layer: 256, acoustic pulse: 128, mixture: 192 by default)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary lines (eight-species mixture, ensemble) of the default run")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-field errors against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["acoustic", "ensemble", "mixture"], default="acoustic",
-                    help="acoustic: the 128^3 binary pulse (default line); ensemble: 64 uneven ternary "
-                         "domains in one batched launch (BF16); mixture: M-species (default 8) random "
-                         "mixture on an n^3 grid (default 192), FP32 against BF16 + learned closure")
+    ap.add_argument("--workload", choices=["shear", "acoustic", "ensemble", "mixture"], default="shear",
+                    help="shear: the 256^3 two-component shear layer (default line); acoustic: the 128^3 "
+                         "binary pulse; ensemble: 64 uneven ternary domains in one batched launch (BF16); "
+                         "mixture: M-species (default 8) random mixture on an n^3 grid (default 192), FP32 "
+                         "against BF16 and BF16 + learned closure")
     ap.add_argument("--M", type=int, default=8, help="species of the mixture workload")
     ap.add_argument("--no-chosen-form", action="store_true",
                     help="skip the BF16-storage / learned-closure comparison on the same workload")
-    ap.add_argument("--oracle-sample", nargs=2, type=int, metavar=("EDGE", "STEPS"),
+    ap.add_argument("--oracle-sample", nargs=3, metavar=("WORKLOAD", "EDGE", "STEPS"),
                     help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -79,11 +87,21 @@ def _job_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
 # ---------------------------------------------------------------------------
 # Oracle timing (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_sample_worker(edge: int, steps: int, warmup: int = 1):
+def _workload(name: str, n: int):
+    """The bench workloads (input recipes only; workloads.py)."""
+    from paper_2004_11286_gb300 import workloads as W
+    if name == "shear":
+        return W.shear_layer(n=n)
+    if name == "acoustic":
+        return W.acoustic_pulse(n=n, sigma=6.0 * n / 128.0)
+    raise ValueError(name)
+
+
+def _oracle_sample_worker(name: str, edge: int, steps: int, warmup: int = 1):
     import numpy as np
     import oracle as O
     from paper_2004_11286_gb300 import workloads as W
-    wl = W.acoustic_pulse(n=edge, sigma=6.0 * edge / 128.0)
+    wl = _workload(name, edge)
     prm = O.Params(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, slaved=W.slaved_species(wl))
     pops = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm)
     for _ in range(warmup):
@@ -96,24 +114,50 @@ def _oracle_sample_worker(edge: int, steps: int, warmup: int = 1):
     return dict(nodes=wl.nodes, steps=steps, seconds=dt, mlups=wl.nodes * steps / dt / 1e6)
 
 
-def _run_oracle_subprocess(edge: int, steps: int, timeout: float = 900.0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(edge), str(steps)],
-                       capture_output=True, text=True, env=env, timeout=timeout)
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                CUDA_VISIBLE_DEVICES="")
+
+
+def _run_oracle_subprocess(name: str, edge: int, steps: int, timeout: float = 900.0):
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", name, str(edge), str(steps)],
+                       capture_output=True, text=True, env=_oracle_env(), timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def _cpu_baseline(target_seconds: float = 15.0):
-    cal = _run_oracle_subprocess(16, 2)
+def _run_oracle_parallel(name: str, edge: int, steps: int, procs: int, timeout: float = 900.0):
+    """`procs` independent single-threaded oracle processes on the same
+    sample at once (one per host core): whole-host throughput = all their
+    lattice updates over the slowest one's time."""
+    ps = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-sample", name, str(edge), str(steps)],
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=_oracle_env())
+          for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate(timeout=timeout)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    secs = max(r["seconds"] for r in res)
+    ups = sum(r["nodes"] * r["steps"] for r in res)
+    return dict(mlups=ups / secs / 1e6, seconds=secs, procs=procs, nodes=res[0]["nodes"], steps=steps)
+
+
+def _cpu_baseline(name: str, target_seconds: float = 15.0):
+    cal = _run_oracle_subprocess(name, 16, 2)
     per_node_step = cal["seconds"] / (cal["nodes"] * cal["steps"])
-    edge, steps = 48, max(2, int(target_seconds / (per_node_step * 48 ** 3)))
-    res = _run_oracle_subprocess(edge, steps)
-    return {"value": round(res["mlups"], 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"acoustic pulse recipe on a {edge}^3 periodic grid, {steps} steps, "
-                      f"FP64 NumPy oracle, one thread ({res['seconds']:.1f} s)"}
+    edge = 32
+    steps = max(2, int(target_seconds / (per_node_step * edge ** 3)))
+    one = _run_oracle_subprocess(name, edge, steps)
+    cores = os.cpu_count() or 1
+    allc = _run_oracle_parallel(name, edge, steps, cores)
+    return {"value": round(allc["mlups"], 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": round(one["mlups"], 5),
+            "sample": f"{name} recipe on a {edge}^3 periodic grid, {steps} steps, FP64 NumPy oracle: "
+                      f"{cores} single-threaded processes at once on the host's {cores} cores "
+                      f"({allc['seconds']:.1f} s), and one alone ({one['seconds']:.1f} s, `one_core`)"}
 
 
 # ---------------------------------------------------------------------------
@@ -200,15 +244,15 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str, precision: str, M: int, nodes: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def _recorded_traffic(kernel: str, precision: str, M: int, nodes: int, workload: str = "shear"):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get(f"{kernel}/{precision}/M{M}")
+    e = d.get(f"{workload}/{kernel}/{precision}/M{M}")
     if not e or e.get("source_hash") != _kernel_source_hash():
         return None
     return float(e["bytes_per_node"]) * nodes
@@ -219,13 +263,16 @@ def _algorithmic_bytes(M: int, precision: str):
     b = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
     bs = 8 if precision == "fp64" else 4
     S = M + 2
+    # 16-bit storage: each node's equilibrium record (rec_w floats) written
+    # once and read once (its receivers gather it from L1/L2)
+    rec = 2 * 4 * (8 + ((1 + M + 3) // 4) * 4) if b == 2 else 0
     return {
         # every population read + written once; the senders' deferred terms
         # (X, K, theta) read once per node; this node's 7 side fields written
-        "collide_stream": 2 * 27 * S * b + 7 * bs + 7 * bs,
+        "collide_stream": 2 * 27 * S * b + 7 * bs + 7 * bs + rec,
         "grad_GK": 7 * bs + 7 * bs,                 # Phi, c_omega, C_p, s, theta -> G, K, theta
         "grad_X": 3 * bs + 3 * bs,                  # G -> X
-        "step": 2 * 27 * S * b + 2 * 5 * bs,        # method minimum: populations once + side fields once
+        "step": 2 * 27 * S * b + 2 * 5 * bs + rec,  # method minimum: populations once + side fields once
     }
 
 
@@ -357,13 +404,16 @@ def _bench_mixture(a, dev):
     h = binding.from_workload(wl, precision="fp32", slaved=slaved, device=dev)
     h.init_fields(wl.X, wl.u, wl.T, wl.P)
     h.step(a.warmup)
+    # 2^21 (2.1e6) training pairs the exact method generates from this
+    # workload: 8 states 20 steps apart, 2^18 random nodes of each
     feats, tgts = [], []
-    for _ in range(3):
+    for _ in range(8):
         h.step(20)
         f, g = h.closure_samples()
         idx = torch.randperm(N, generator=torch.Generator().manual_seed(len(feats)))[: 1 << 18].to(dev)
-        feats.append(f[idx])
-        tgts.append(g[idx])
+        feats.append(f[idx].clone())
+        tgts.append(g[idx].clone())
+        del f, g
     ms = _timed_steps(h.step, h.stream, a.steps)
     h.close()
     alg32 = _algorithmic_bytes(M, "fp32")["step"]
@@ -406,35 +456,97 @@ def _bench_mixture(a, dev):
 
 
 # ---------------------------------------------------------------------------
+def _parity(name: str, dev):
+    """Per-field errors against the FP64 oracle on a reduced copy of the
+    workload (same recipe and constants, a grid the oracle steps in seconds),
+    for plain FP32, BF16 storage and BF16 + the learned closure (trained on
+    this copy's own exact pairs).  rho, T, P relative; u relative to
+    max(||u||, 1e-3 c_s); X absolute (the norms of the parity tests)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2004_11286_gb300 import binding, workloads as W
+    if name == "shear":
+        wl, steps = W.shear_layer(shape=(16, 64, 16)), 20
+    else:
+        wl, steps = W.acoustic_pulse(shape=(12, 14, 16), sigma=2.0), 300
+    slaved = W.slaved_species(wl)
+    prm = O.Params(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, slaved=slaved)
+    mac = O.macroscopic(O.run(O.init_populations(wl.X, wl.u, wl.T, wl.P, prm), prm, steps), prm)
+    mbar = float(np.dot(wl.X.reshape(wl.M, -1).mean(axis=1), wl.molar_mass))
+    cs = float(np.sqrt(1.4 * wl.T.mean() / mbar))
+
+    def errs(h):
+        g = h.moments_dict()
+        r = lambda k, fl=0.0: float(np.abs(g[k] - mac[k]).max() / max(float(np.abs(mac[k]).max()), fl))
+        return {"rho": r("rho"), "u": r("u", 1e-3 * cs), "T": r("T"), "P": r("P"),
+                "X": float(np.abs(g["X"] - mac["X"]).max())}
+
+    out = {"workload": f"{name} recipe on {'x'.join(map(str, wl.shape))}, {steps} steps", "norm":
+           "max|a-b| / max(|b|_inf, floor); floor 1e-3 c_s for u; X absolute"}
+    for prec in ("fp32", "bf16"):
+        h = binding.from_workload(wl, precision=prec, slaved=slaved, device=dev)
+        h.init_fields(wl.X, wl.u, wl.T, wl.P)
+        h.step(steps)
+        out[prec] = {k: float(f"{v:.3g}") for k, v in errs(h).items()}
+        h.close()
+    hs = binding.from_workload(wl, precision="fp32", slaved=slaved, device=dev)
+    hs.init_fields(wl.X, wl.u, wl.T, wl.P)
+    feats, tgts = [], []
+    for _ in range(4):
+        hs.step(max(1, steps // 4))
+        f, g = hs.closure_samples()
+        feats.append(f)
+        tgts.append(g)
+    hs.close()
+    feat, tgt = torch.cat(feats).contiguous(), torch.cat(tgts).contiguous()
+    hm = binding.from_workload(wl, precision="bf16", slaved=slaved, closure="mlp", device=dev)
+    hm.set_closure_weights(W.closure_initial_weights(wl.M, seed=1))
+    hm.closure_train(feat, tgt, batch=2048, steps=2000, lr=1e-3)
+    hm.closure_train(feat, tgt, batch=2048, steps=1000, lr=2e-4)
+    hm.init_fields(wl.X, wl.u, wl.T, wl.P)
+    hm.closure_stats(reset=True)
+    hm.step(steps)
+    acc, fb = hm.closure_stats()
+    out["bf16_learned_closure"] = {k: float(f"{v:.3g}") for k, v in errs(hm).items()}
+    out["bf16_learned_closure"]["accepted_fraction"] = round(acc / max(1, acc + fb), 4)
+    hm.close()
+    return out
+
+
 def main():
     a = _args()
-    if a.n is None and a.workload == "acoustic":
-        a.n = 128
+    if a.n is None:
+        a.n = {"shear": 256, "acoustic": 128}.get(a.workload)
     if a.oracle_sample:
-        print(json.dumps(_oracle_sample_worker(*a.oracle_sample)))
+        name, edge, steps = a.oracle_sample
+        print(json.dumps(_oracle_sample_worker(name, int(edge), int(steps))))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    name = a.workload if a.workload in ("shear", "acoustic") else "shear"
 
     if a.impl == "reference":
         if rank != 0:
             return
-        cal = _run_oracle_subprocess(16, 2)
+        cal = _run_oracle_subprocess(name, 16, 2)
         per = cal["seconds"] / (cal["nodes"] * cal["steps"])
-        budget = 150.0 / max(1, a.steps + a.warmup)
-        edge = int(max(8, min(a.n, round((budget / per) ** (1.0 / 3.0)))))
-        res = _run_oracle_subprocess(edge, a.steps, timeout=1800)
+        budget = 120.0 / max(1, a.steps + a.warmup)
+        # at most 48^3 per process, so one copy per core stays within the host's memory
+        edge = int(max(8, min(a.n or 256, 48, round((budget / per) ** (1.0 / 3.0)))))
+        cores = os.cpu_count() or 1
+        res = _run_oracle_parallel(name, edge, a.steps, cores, timeout=1800)
         v = round(res["mlups"], 6)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
                 "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": round(1e3 * res["seconds"] / a.steps, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"acoustic pulse, M=2 (m=4,40), {edge}^3 periodic sample of the "
-                                       f"{a.n}^3 workload", "precision": "fp64"},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{edge}^3 periodic grid, {a.steps} steps"},
+                "config": {"workload": f"{name} recipe, {edge}^3 periodic sample of the {a.n}^3 workload, "
+                                       f"{cores} single-threaded oracle processes", "precision": "fp64"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{edge}^3 periodic grid, {a.steps} steps, one copy per core"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -454,13 +566,13 @@ def main():
     if world > 1:
         dist.barrier()
     binding.load_library()
-    if a.workload != "acoustic":
+    if a.workload in ("ensemble", "mixture"):
         line = _bench_ensemble(a, dev) if a.workload == "ensemble" else _bench_mixture(a, dev)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
 
-    wl = W.acoustic_pulse(n=a.n)
+    wl = _workload(name, a.n)
     slaved = W.slaved_species(wl)
     h = binding.LbmMix(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, shape=wl.shape,
                        precision=a.precision, slaved=slaved, R_U=wl.R_U, device=dev)
@@ -470,6 +582,7 @@ def main():
     Td = torch.from_numpy(wl.T.ravel()).to(dev)
     Pd = torch.from_numpy(wl.P.ravel()).to(dev)
     h.init_fields(Xd, ud, Td, Pd)
+    del Xd, ud, Td, Pd
     h.step(a.warmup)
     h.synchronize()
 
@@ -508,7 +621,7 @@ def main():
     peak, peak_src = _peaks()
     achieved = alg[dom] * N / (dom_ms * 1e-3) / 1e9
     step_alg_gbs = alg["step"] * N * a.steps / (elapsed_ms * 1e-3) / 1e9
-    traffic = _recorded_traffic(dom, a.precision, wl.M, N)
+    traffic = _recorded_traffic(dom, a.precision, wl.M, N, name)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
                 "peak_source": peak_src + (" (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
@@ -544,34 +657,56 @@ def main():
                "h2d_bytes_per_step": round(h2d / a.steps, 1), "d2h_bytes_per_step": round(d2h / a.steps, 1),
                "note": "init_fields from pinned host fields + step(K) + get_moments to pinned host + "
                        "diagnostics, host wall clock"}
+        del Xp, up, Tp, Pp, outp
+    h.close()
+    torch.cuda.empty_cache()
 
     chosen = None
     if not a.no_chosen_form and a.precision == "fp32":
-        chosen = _chosen_form(wl, dev, min(a.steps, 500), peak)
+        chosen = _chosen_form(wl, dev, min(a.steps, 200), peak)
+
+    parity = None
+    if not a.no_parity and rank == 0:
+        parity = _parity(name, dev)
+
+    secondary = None
+    if not a.no_secondary and world == 1 and rank == 0:
+        torch.cuda.empty_cache()
+        sa = argparse.Namespace(**vars(a))
+        sa.steps, sa.warmup, sa.n, sa.M = min(a.steps, 60), 5, 192, 8
+        secondary = {"mixture_M8_192cube": _bench_mixture(sa, dev)}
+        torch.cuda.empty_cache()
+        sa.steps = min(a.steps, 100)
+        secondary["ensemble_64_domains"] = _bench_ensemble(sa, dev)
+        for v in secondary.values():
+            for k in ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data"):
+                v.pop(k, None)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and world == 1:
         try:
-            cpu = _cpu_baseline()
+            cpu = _cpu_baseline(name)
         except Exception as ex:  # the baseline is reported, never required
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"[:300]}
 
     if rank == 0:
+        desc = {"shear": f"two-component Kelvin-Helmholtz shear layer, {a.n}^3 periodic D3Q27, M=2 (m=2,28), "
+                         "tanh velocity and composition profiles, Mach 0.3",
+                "acoustic": f"binary acoustic pulse, {a.n}^3 periodic D3Q27, M=2 (m=4,40)"}[name]
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": round(elapsed_ms / a.steps, 5), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision,
                 "data": "synthetic",
-                "config": {"workload": f"binary acoustic pulse, {a.n}^3 periodic D3Q27, M=2 (m=4,40), "
-                                       f"species+f+g = {27 * (wl.M + 2)} populations/node, {a.precision}",
+                "config": {"workload": f"{desc}, species+f+g = {27 * (wl.M + 2)} populations/node, {a.precision}",
                            "grid": list(wl.shape), "M": wl.M, "precision": a.precision,
                            "l2": "inputs larger than L2 (%.0f MB of populations), no flush" %
                                  (27 * (wl.M + 2) * N * {"fp64": 8, "fp32": 4}.get(a.precision, 2) / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "chosen_form": chosen,
+                "chosen_form": chosen, "parity": parity, "secondary": secondary,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -61,13 +61,23 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+/* Precision of the populations in memory and of the arithmetic:
+ *   FP64, FP32: stored as deviations from one reference rest state, arithmetic
+ *     in the same type;
+ *   FP16_STORE, BF16_STORE: FP32 arithmetic; each population stored in 16 bits
+ *     as its deviation from the local equilibrium of the node that wrote it
+ *     (f - f^eq of Eqs. 27eq, feq, gieq, the node's lattice weights at its
+ *     velocity and temperature times its density), scaled per lattice.  Each
+ *     collision also writes a per-node FP32 record of the quantities its
+ *     equilibria are built from, which the receivers of its populations read
+ *     (in the scratch buffer, see lbm_mix_required_bytes). */
 enum { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_FP16_STORE = 2, LBM_PREC_BF16_STORE = 3 };
 enum { LBM_COUPLE_STRONG = 0, LBM_COUPLE_WEAK = 1 };
 enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
 
 /* Problem statement as the paper poses it (Secs. 2.1, 2.3, 3.1, 3.3, 3.5). */
 typedef struct {
-  int M;                      /* number of species: kernels exist for 1, 2, 3, 4 and 8 */
+  int M;                      /* number of species, 1..8 */
   const double* molar_mass;   /* [M] m_a > 0; R_a = R_U / m_a (Eq. Ra) */
   const double* cv_molar;     /* [M] C-bar_{a,v} / R_U > 0 (Sec. 3.1, constant) */
   const double* D;            /* [M*M] row-major, symmetric binary diffusivities
@@ -121,7 +131,10 @@ LBM_API lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lb
  * FP32 otherwise: Phi_alpha, 1/omega-1/2, C_p, the q^corr scale and theta
  * written by each collision; G_alpha, K_alpha and the sender's theta; X_alpha
  * of Eq. Xalpha).  The scratch also carries the previous step's non-local
- * terms, which the next step applies to the arriving populations. */
+ * terms, which the next step applies to the arriving populations.  With
+ * 16-bit storage the scratch holds, after the side fields (rounded up to 256
+ * bytes), two buffers of per-node equilibrium records of
+ * 4 * (8 + 4*ceil((M+1)/4) + (weak coupling ? 4 : 0)) bytes each. */
 LBM_API lbm_status lbm_mix_required_bytes(lbm_mix_t h, size_t* pops_bytes, size_t* scratch_bytes);
 
 /* Binds caller-owned device buffers (at least the required sizes, 256-byte

@@ -1,0 +1,3 @@
+// Kernels for M = 6 species, FP32 arithmetic with BF16 storage.
+#include "lbm_inst.cuh"
+LBM_INSTANTIATE(6, bf16, float, __nv_bfloat16)

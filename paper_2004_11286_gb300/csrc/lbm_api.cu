@@ -9,6 +9,7 @@
 
 #include "../../include/lbm_mix.h"
 #include "lbm_device.cuh"
+#include "lbm_eqcodec.cuh"
 #include "lbm_dispatch.h"
 #include "lbm_train.h"
 
@@ -31,6 +32,9 @@ const lbm::KernelSet* select_kernels(int M, int prec) {
     LBM_PICK(2)
     LBM_PICK(3)
     LBM_PICK(4)
+    LBM_PICK(5)
+    LBM_PICK(6)
+    LBM_PICK(7)
     LBM_PICK(8)
     default: return nullptr;
   }
@@ -58,6 +62,9 @@ void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   for (int L = 0; L < lbm::MAXM + 2; ++L) {
     d.RL[L] = (Real)s.RL[L]; d.scale[L] = (Real)s.scale[L]; d.inv_scale[L] = (Real)s.inv_scale[L];
   }
+  for (int L = 0; L < lbm::MAXM + 2; ++L)
+    for (int k = 0; k < 4; ++k) d.bref[L][k] = (Real)s.bref[L][k];
+  d.rec_w = s.rec_w;
   for (int a = 0; a < lbm::MAXM; ++a) d.Yr[a] = (Real)s.Yr[a];
   d.Tr = (Real)s.Tr; d.Rr = (Real)s.Rr; d.thr = (Real)s.thr; d.Pr = (Real)s.Pr; d.Cvr = (Real)s.Cvr;
   d.cE = (Real)s.cE; d.cPi = (Real)s.cPi; d.cS = (Real)s.cS; d.Rsp = (Real)s.Rsp;
@@ -178,7 +185,11 @@ struct lbm_mix {
   long long z_rows = 0;
 
   size_t need_pops() const { return (size_t)(M + 2) * 27 * (size_t)N * store_elem_bytes(prec); }
-  size_t need_scratch() const { return (size_t)lbm::NSIDE * (size_t)N * side_elem_bytes(prec); }
+  // side planes, then (16-bit storage) the two buffers of equilibrium records
+  size_t need_scratch() const {
+    if (p64.rec_w == 0) return (size_t)lbm::NSIDE * (size_t)N * side_elem_bytes(prec);
+    return ((size_t)lbm::eq_rec_offset(N) + 2 * (size_t)p64.rec_w * (size_t)N) * sizeof(float);
+  }
   lbm::LaunchCtx ctx() {
     lbm::LaunchCtx c;
     c.N = N; c.stream = stream; c.pops = pops; c.side = scratch; c.err = d_err;
@@ -251,15 +262,24 @@ struct lbm_mix {
       const double BZ = c2 == 0 ? 3.0 * Z : (c2 == 1 ? -0.5 * Z : 0.0);
       base[(M + 1) * 27 + i] = W(i, th) * E + BZ;
     }
-    for (int L = 0; L < lbm::MAXM + 2; ++L) { d.RL[L] = 0.0; d.scale[L] = 1.0; d.inv_scale[L] = 1.0; }
+    for (int L = 0; L < lbm::MAXM + 2; ++L) {
+      d.RL[L] = 0.0; d.scale[L] = 1.0; d.inv_scale[L] = 1.0;
+      for (int k = 0; k < 4; ++k) d.bref[L][k] = 0.0;
+    }
     for (int L = 0; L < S; ++L) {
       double sum = 0.0;
       for (int i = 0; i < 27; ++i) sum += base[L * 27 + i];
       d.RL[L] = sum;
+      // 16-bit storage holds the non-equilibrium part f - f^eq of each
+      // population, scaled per lattice: FP16 by 2^12 / RL (the part is a
+      // small fraction of RL, so this keeps it in FP16's normal range),
+      // BF16 by 1 / RL (its exponent range makes the scale immaterial).
       if (prec == LBM_PREC_FP16_STORE || prec == LBM_PREC_BF16_STORE) {
-        d.scale[L] = 1.0 / std::fabs(sum);
-        d.inv_scale[L] = std::fabs(sum);
+        const double s = (prec == LBM_PREC_FP16_STORE ? 4096.0 : 1.0) / std::fabs(sum);
+        d.scale[L] = s;
+        d.inv_scale[L] = 1.0 / s;
       }
+      for (int i = 0; i < 27; ++i) d.bref[L][lbm::c2_of(i)] = base[L * 27 + i];
     }
     double Rsp = 0.0;
     for (int a = 0; a < M; ++a) Rsp += d.RL[a];
@@ -618,6 +638,8 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
       d.Cab64[a][b] = d.Cab[a][b];
     }
   d.rho_eps = 1e-14;
+  const bool store16 = p->precision == LBM_PREC_FP16_STORE || p->precision == LBM_PREC_BF16_STORE;
+  d.rec_w = store16 ? lbm::eq_rec_width(M, d.weak) : 0;
   fill_params<float>(h->p32, d);
   h->p32.rho_eps = 1e-7f;
 
@@ -712,7 +734,7 @@ lbm_status lbm_mix_init_fields(lbm_mix_t h, const double* X, const double* u, co
   if ((s = h->reference_from_fields(dX, dT, dP)) != LBM_OK) return s;
   if ((s = h->clear_pending()) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->init(h->ctx(), dX, du, dT, dP), "init kernel")) != LBM_OK) return s;
-  h->launches += 1;
+  h->launches += h->ks->setup_launches;
   h->steps = 0;
   h->initialized = true;
   if (host_ptrs) return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
@@ -801,7 +823,7 @@ lbm_status lbm_mix_set_populations(lbm_mix_t h, const double* in, int host_ptrs)
   if (!h->has_reference && (s = h->reference_from_pops(src)) != LBM_OK) return s;
   if ((s = h->clear_pending()) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->set_pops(h->ctx(), (int)(h->steps & 1), src), "set_populations kernel")) != LBM_OK) return s;
-  h->launches += 1;
+  h->launches += h->ks->setup_launches;
   h->initialized = true;
   if (host_ptrs) return h->cuda(cudaStreamSynchronize(h->stream), "synchronize");
   return LBM_OK;

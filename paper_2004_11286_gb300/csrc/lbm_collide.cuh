@@ -21,11 +21,10 @@ namespace lbm {
 #ifndef LBM_COLLIDE_BS
 #define LBM_COLLIDE_BS 128
 #endif
-// The stage holds the momentum and energy populations (with their deferred
-// terms added) in the arithmetic type and the species populations as stored:
-// 16-bit storage stages them raw and decodes on use.
+// The stage holds every population in the arithmetic type, decoded and with
+// its deferred terms added.
 template <class Real, class Store>
-using StageSp = typename std::conditional<(sizeof(Store) < sizeof(Real)), Store, Real>::type;
+using StageSp = Real;
 template <int M, class Real, class Store>
 constexpr long long stage_per_node() {
   return (long long)M * 27 * sizeof(StageSp<Real, Store>) + 2LL * 27 * sizeof(Real);
@@ -144,7 +143,9 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
                                              unsigned char* smem_raw) {
   constexpr int BS = collide_block<M, Real, CL, Store>();
   using SpT = StageSp<Real, Store>;
-  static_assert(!LD || std::is_same<SpT, Real>::value, "bulk loads stage the stored type");
+  // 16-bit storage: shifted deviations from the senders' equilibria (lbm_eqcodec.cuh)
+  constexpr bool EQ = kEqCodec<Store, Real>;
+  static_assert(!LD || std::is_same<Store, Real>::value, "bulk loads stage the stored type");
   static_assert(!(LD && WALL), "walls use the register-load path");
   // Stage, thread-private columns: species [M*27][BS] (SpT), then f, g [2*27][BS] (Real).
   SpT* const sps = reinterpret_cast<SpT*>(smem_raw);
@@ -193,11 +194,8 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       return pl[tid];
     }
   };
-  auto species_val = [&](int a, int i, int cx) -> Real {
-    if constexpr (std::is_same<SpT, Real>::value) return cell(a, i, cx);
-    else { (void)cx; return codec_decode<Store, Real>(p, sps[(a * Q + i) * BS + tid], a); }
-  };
-  auto accumulate = [&](auto I_, const Real (&v)[M], Real fv, Real gv) {
+  auto species_val = [&](int a, int i, int cx) -> Real { return cell(a, i, cx); };
+  auto accumulate = [&](auto I_, const Real* v, Real fv, Real gv) {
     constexpr int i = decltype(I_)::value;
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
 #pragma unroll
@@ -260,17 +258,19 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       long long node; int slot;
       aa_read_loc<WALL>(PAR, nb, n, i, node, slot);
       Real cf = Real(0), cg = Real(0);
-      if constexpr (i != 13) deferred_terms<Real, i, WALL>(side, N, nb, n, cf, cg);
-      Real v[M];
+      Real v[M + 2];   // species, then the shifts of f and g (zero without the shifted codec)
+      if constexpr (EQ) eq_incoming<M, i, WALL>(p, side, nb, n, PAR, cf, cg, v);
+      else if constexpr (i != 13) deferred_terms<Real, i, WALL>(side, N, nb, n, cf, cg);
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        const Store raw = pops[(a * Q + slot) * N + node];
-        v[a] = codec_decode<Store, Real>(p, raw, a);
-        sps[(a * Q + i) * BS + tid] = std::is_same<SpT, Real>::value ? (SpT)v[a] : (SpT)raw;
+        const Real d = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+        if constexpr (EQ) v[a] += d; else v[a] = d;
+        sps[(a * Q + i) * BS + tid] = v[a];
       }
-      const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+      Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+      Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+      if constexpr (EQ) { fv += v[M]; gv += v[M + 1]; }
       sfg[i * BS + tid] = fv;
-      const Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
       sfg[(Q + i) * BS + tid] = gv;
       accumulate(I_, v, fv, gv);
     });
@@ -406,13 +406,16 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
         s_f += e;
         const Real fv = cell(M, i, cx_of(i));
-        if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * (e - fv));
+        const Real out = fv + om * (e - fv);
+        if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, EQ ? out - e : out);
       }
     });
     long long node; int slot;
     aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
     const Real fv = cell(M, 13, 0);
-    if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, fv + om * ((rho_dev - s_f) - fv));
+    const Real e13 = rho_dev - s_f;
+    const Real out = fv + om * (e13 - fv);
+    if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, EQ ? out - e13 : out);
   }
 
   // a9: energy lattice.  With N = R^eq - rho E theta I, Eqs. (geq2mom),
@@ -442,7 +445,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 #pragma unroll
       for (int c = 0; c < 3; ++c) dZ[c] = zb + z1 * Gc * u[c] * u[c];
     }
-    Real mvec[3];
+    Real mvec[3], qt[3];
     {
       Real dP6[6];   // Pi - P^eq from deviations
       dP6[0] = p.cPi + S[0] - th.dP - rho * u[0] * u[0];
@@ -452,6 +455,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       dP6[4] = S[4] - rho * u[0] * u[2];
       dP6[5] = S[5] - rho * u[1] * u[2];
       const Real qeq[3] = {hk * j[0], hk * j[1], hk * j[2]};
+      qt[0] = qeq[0] * inv_theta; qt[1] = qeq[1] * inv_theta; qt[2] = qeq[2] * inv_theta;
       Real qb[3];
       qb[0] = q[0] - (u[0] * dP6[0] + u[1] * dP6[3] + u[2] * dP6[4]);
       qb[1] = q[1] - (u[0] * dP6[3] + u[1] * dP6[1] + u[2] * dP6[5]);
@@ -467,6 +471,19 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       const Real c1 = om1 * T * rY, dw = om - om1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) mvec[c] = (om * qeq[c] + dw * (qb[c] - qeq[c]) + c1 * hyv[c]) * inv_theta;
+    }
+    if constexpr (EQ) {
+      // this node's equilibrium record, for the receivers of its populations
+      if (active) {
+        EqRec<M> r;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { r.u[c] = u[c]; r.usp[c] = th.u_sp[c]; }
+        r.dth = dth; r.dT = th.dT; r.drho = rho_dev; r.drhoE = rhoE_dev;
+        r.Gq = Gc * inv_theta; r.hq = hk * rho * inv_theta;
+#pragma unroll
+        for (int a = 0; a < M; ++a) r.ra[a] = th.rho_a_dev[a];
+        store_rec<M>(eq_rec_buf(side, N, p.rec_w, PAR), n, p.rec_w, p.weak, r);
+      }
     }
     const Real w0 = Real(1) - theta, w1 = Real(0.5) * theta;          // Eq. (w0)
     const Real r0 = Real(1) - thr, r1 = Real(0.5) * thr;
@@ -492,16 +509,18 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
         s_g += e;
         const Real gv = cell(M + 1, i, cx);
+        const Real out = gv + om * (e - gv) + wi * dotc<Real, i>(mvec);
         if (active)
           codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
-                                   gv + om * (e - gv) + wi * dotc<Real, i>(mvec));
+                                   EQ ? out - (e + wi * dotc<Real, i>(qt)) : out);
       }
     });
     long long node; int slot;
     aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
     const Real gv = cell(M + 1, 13, 0);
-    if (active)
-      codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, gv + om * ((rhoE_dev - s_g) - gv));
+    const Real e13 = rhoE_dev - s_g;
+    const Real out = gv + om * (e13 - gv);
+    if (active) codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, EQ ? out - e13 : out);
   }
 
   // a7: species, Eqs. (SMlbm), (fstar1).  Equilibrium deviation
@@ -565,9 +584,8 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         const Real e = th.rho_a[a] * d + th.rho_a_dev[a] * (rx * ry * pf_r<Real>(cz, zr[a]));
         s_e[a] += e; s_F[a] += F;
         const Real kv = species_val(a, i, cx);
-        if (active)
-          codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
-                                   kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F);
+        const Real out = kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F;
+        if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
       }
     };
     if constexpr (M >= LBM_SPECIES_LOOP_MIN_M) {
@@ -602,9 +620,8 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];
       const Real kv = species_val(a, 13, 0);
-      if (active)
-        codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a,
-                                 kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a]);
+      const Real out = kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a];
+      if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
     }
   }
   if constexpr (CL) mlp.teardown();

@@ -81,6 +81,11 @@ struct DevParams {
   Real cS;               // RL[f] - sum_a RL[a]
   Real Rsp;              // sum_a RL[a]
   Real scale[MAXM + 2], inv_scale[MAXM + 2];   // storage scale of reduced-precision modes
+  // Reduced-precision storage (lbm_eqcodec.cuh): the reference rest
+  // equilibria b_L,i by lattice and |c_i|^2, and the width in floats of the
+  // per-node equilibrium record (0 in the FP64 and FP32 modes).
+  Real bref[MAXM + 2][4];
+  int rec_w;
 };
 
 // ---------------------------------------------------------------------------

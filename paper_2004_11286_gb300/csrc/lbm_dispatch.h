@@ -56,6 +56,7 @@ struct KernelSet {
   cudaError_t (*batch_prepare)();
   cudaError_t (*batch_step)(const BatchCtx&, int parity);
   int launches_per_step;
+  int setup_launches;                        // kernels of init_fields / set_populations
   int collide_bs;                            // nodes per collide block
   int mlp_F, mlp_O, mlp_nw, mlp_img_bytes;   // network sizes for this species count
   int mlp_step_ok;                           // the step can run the learned closure
@@ -71,6 +72,9 @@ LBM_DECLARE_SETS(1)
 LBM_DECLARE_SETS(2)
 LBM_DECLARE_SETS(3)
 LBM_DECLARE_SETS(4)
+LBM_DECLARE_SETS(5)
+LBM_DECLARE_SETS(6)
+LBM_DECLARE_SETS(7)
 LBM_DECLARE_SETS(8)
 #undef LBM_DECLARE_SETS
 

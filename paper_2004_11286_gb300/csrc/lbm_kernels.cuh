@@ -24,14 +24,58 @@ namespace lbm {
 // Equilibrium initialisation (Eqs. 27eq, fixed, feq, gieq), evaluated in FP64
 // as full populations and stored as deviations from the base table.
 // ---------------------------------------------------------------------------
+// 16-bit storage: the record of every node from the fields (into buffer 1,
+// which the first step, of parity 0, reads).
+template <int M>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+init_rec_kernel(const DevParams<double> p, float* __restrict__ side, const double* __restrict__ Xin,
+                const double* __restrict__ uin, const double* __restrict__ Tin, const double* __restrict__ Pin) {
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  double X[M], u[3], m = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) { X[a] = Xin[a * N + n]; m += X[a] * p.mass[a]; }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = uin[c * N + n];
+  const double T = Tin[n], rho = Pin[n] * m / (p.R_U * T);
+  double ra[M], Cv = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    const double Y = X[a] * p.mass[a] / m;
+    ra[a] = Y * rho;
+    Cv += Y * p.Cv_a[a];
+  }
+  const double j[3] = {rho * u[0], rho * u[1], rho * u[2]};
+  const double rhoE = rho * (Cv * T + 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  store_rec<M>(eq_rec_buf(side, N, p.rec_w, 1), n, p.rec_w, p.weak, eq_record64<M>(p, ra, rho, j, rhoE, u));
+}
+
+// With 16-bit storage the stored value of each population is its deviation
+// minus the shift of its sender's record (init_rec_kernel; p32 gives the
+// FP32 constants the shifts are formed with).
 template <int M, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-init_kernel(const DevParams<double> p, Store* __restrict__ pops, const double* __restrict__ base,
+init_kernel(const DevParams<double> p, const DevParams<float> p32, Store* __restrict__ pops,
+            const float* __restrict__ side, const double* __restrict__ base,
             const double* __restrict__ Xin, const double* __restrict__ uin,
             const double* __restrict__ Tin, const double* __restrict__ Pin) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
+  // shifts [i][L] of the senders' equilibria (zero without the shifted codec)
+  float sh[Q][M + 2];
+  if constexpr (kEqCodec<Store, float>) {
+    const Nbr nb = make_nbr(p, n);
+    static_for<0, Q>([&](auto I_) {
+      constexpr int i = decltype(I_)::value;
+      float cf, cg;
+      eq_incoming<M, i, true>(p32, side, nb, n, 0, cf, cg, sh[i]);
+    });
+  } else {
+    for (int i = 0; i < Q; ++i)
+      for (int L = 0; L < M + 2; ++L) sh[i][L] = 0.0f;
+  }
   double X[M], u[3];
 #pragma unroll
   for (int a = 0; a < M; ++a) X[a] = Xin[a * N + n];
@@ -59,7 +103,7 @@ init_kernel(const DevParams<double> p, Store* __restrict__ pops, const double* _
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double v = ra * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i));
-      codec_store<Store, double>(p, pops, (a * Q + i) * N + n, a, v - base[a * Q + i]);
+      codec_store<Store, double>(p, pops, (a * Q + i) * N + n, a, v - base[a * Q + i] - (double)sh[i][a]);
     }
   }
   {
@@ -68,7 +112,7 @@ init_kernel(const DevParams<double> p, Store* __restrict__ pops, const double* _
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double v = rho * tri(tx, cx_of(i)) * tri(ty, cy_of(i)) * tri(tz, cz_of(i));
-      codec_store<Store, double>(p, pops, (M * Q + i) * N + n, M, v - base[M * Q + i]);
+      codec_store<Store, double>(p, pops, (M * Q + i) * N + n, M, v - base[M * Q + i] - (double)sh[i][M]);
     }
   }
   {
@@ -86,7 +130,8 @@ init_kernel(const DevParams<double> p, Store* __restrict__ pops, const double* _
       constexpr int i = decltype(I_)::value;
       const double w = tri(gc.w, cx_of(i)) * tri(gc.w, cy_of(i)) * tri(gc.w, cz_of(i));
       const double v = w * (g_even_part<double, i>(gc) + dotc<double, i>(mt)) + g_BZ<double, i>(gc);
-      codec_store<Store, double>(p, pops, ((M + 1) * Q + i) * N + n, M + 1, v - base[(M + 1) * Q + i]);
+      codec_store<Store, double>(p, pops, ((M + 1) * Q + i) * N + n, M + 1,
+                                 v - base[(M + 1) * Q + i] - (double)sh[i][M + 1]);
     });
   }
 }
@@ -126,16 +171,16 @@ diag_partial_kernel(const DevParams<Real> p, const Store* __restrict__ pops, con
       constexpr int i = decltype(I_)::value;
       long long node; int slot;
       aa_read_loc<true>(parity, nb, n, i, node, slot);
-      Real cf = Real(0), cg = Real(0);
-      if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
+      Real cf, cg, sh[M + 2];
+      incoming_terms<M, Real, Store, i>(p, side, nb, n, parity, cf, cg, sh);
 #pragma unroll
-      for (int a = 0; a < M; ++a) w[a] += codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
-      const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+      for (int a = 0; a < M; ++a) w[a] += codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a) + sh[a];
+      const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf + sh[M];
       w[M] += fv;
       if constexpr (cx_of(i) != 0) w[M + 1] += cx_of(i) * fv;
       if constexpr (cy_of(i) != 0) w[M + 2] += cy_of(i) * fv;
       if constexpr (cz_of(i) != 0) w[M + 3] += cz_of(i) * fv;
-      w[M + 4] += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+      w[M + 4] += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg + sh[M + 1];
     });
 #pragma unroll
     for (int s = 0; s < NV; ++s) v[s] = (double)w[s];
@@ -181,10 +226,13 @@ struct Launch {
   static const DevParams<Real>& P(const LaunchCtx& c) {
     if constexpr (sizeof(Real) == 8) return *c.p64; else return *c.p32;
   }
+  static constexpr bool EQ = kEqCodec<Store, Real>;
   static cudaError_t init(const LaunchCtx& c, const double* X, const double* u, const double* T,
                           const double* Pr) {
+    if constexpr (EQ)
+      init_rec_kernel<M><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(*c.p64, (float*)c.side, X, u, T, Pr);
     init_kernel<M, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        *c.p64, (Store*)c.pops, c.base, X, u, T, Pr);
+        *c.p64, *c.p32, (Store*)c.pops, (const float*)c.side, c.base, X, u, T, Pr);
     return cudaGetLastError();
   }
   template <int CL, int LD, int WALL = 0>
@@ -297,8 +345,11 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t set_pops(const LaunchCtx& c, int parity, const double* in) {
+    if constexpr (EQ)
+      rec_from_pops_kernel<M><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(*c.p64, (float*)c.side,
+                                                                                       1 - parity, in);
     set_pops_kernel<M, Real, Store><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(
-        P(c), (Store*)c.pops, c.base, parity, in);
+        P(c), (Store*)c.pops, (const Real*)c.side, c.base, parity, in);
     return cudaGetLastError();
   }
   static cudaError_t diag(const LaunchCtx& c, int parity, double* d_sums) {
@@ -315,6 +366,7 @@ struct Launch {
     k.samples = &samples; k.mlp_forward = &mlp_forward; k.mlp_pack = &mlp_pack;
     k.batch_prepare = &batch_prepare; k.batch_step = &batch_step;
     k.launches_per_step = 3;
+    k.setup_launches = EQ ? 2 : 1;
     k.collide_bs = collide_block<M, Real, 0, Store>();
     k.mlp_F = MlpDims<M>::F; k.mlp_O = MlpDims<M>::O; k.mlp_nw = MlpDims<M>::NW;
     k.mlp_img_bytes = MlpDims<M>::IMG_BYTES;

@@ -42,12 +42,15 @@ moments_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const Re
     for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
   Real J[M][3];
   sm_solve<M, Real>(p, th, itab, ja, J);
-  out[0 * N + n] = (double)th.rho;
+  // rho, T and P leave as the reference value plus the state's deviation,
+  // summed in FP64, so the output carries the deviation's own precision
+  // rather than the rounding of the full value in the arithmetic type.
+  out[0 * N + n] = (double)p.RL[M] + (double)th.rho_dev;
   out[1 * N + n] = (double)th.u[0];
   out[2 * N + n] = (double)th.u[1];
   out[3 * N + n] = (double)th.u[2];
-  out[4 * N + n] = (double)th.T;
-  out[5 * N + n] = (double)th.P;
+  out[4 * N + n] = (double)p.Tr + (double)th.dT;
+  out[5 * N + n] = (double)p.Pr + (double)th.dP;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     out[(6 + a) * N + n] = (double)(th.m * th.Y[a] * p.inv_mass[a]);
@@ -72,10 +75,10 @@ get_pops_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const R
     constexpr int i = decltype(I_)::value;
     long long node; int slot;
     aa_read_loc<true>(parity, nb, n, i, node, slot);
-    Real cf = Real(0), cg = Real(0);
-    if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
+    Real cf, cg, sh[M + 2];
+    incoming_terms<M, Real, Store, i>(p, side, nb, n, parity, cf, cg, sh);
     for (int L = 0; L < M + 2; ++L) {
-      double v = (double)codec_load<Store, Real>(p, pops, (L * Q + slot) * N + node, L);
+      double v = (double)codec_load<Store, Real>(p, pops, (L * Q + slot) * N + node, L) + (double)sh[L];
       if (L == M) v += (double)cf;
       if (L == M + 1) v += (double)cg;
       out[(L * Q + i) * N + n] = base[L * Q + i] + v;
@@ -83,22 +86,69 @@ get_pops_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const R
   });
 }
 
+// 16-bit storage: each node's equilibrium record (lbm_eqcodec.cuh) from
+// natural-layout full populations, into record buffer `buf`.
+template <int M>
+__global__ void __launch_bounds__(BLOCK_LIGHT)
+rec_from_pops_kernel(const DevParams<double> p, float* __restrict__ side, int buf, const double* __restrict__ in) {
+  const long long n = gtid();
+  if (n >= p.N) return;
+  const long long N = p.N;
+  double ra[M], jsp[3] = {0.0, 0.0, 0.0}, rho = 0.0, j[3] = {0.0, 0.0, 0.0}, rhoE = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) ra[a] = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+    for (int a = 0; a < M; ++a) {
+      const double v = in[(a * Q + i) * N + n];
+      ra[a] += v;
+      for (int d = 0; d < 3; ++d) jsp[d] += c[d] * v;
+    }
+    const double f = in[(M * Q + i) * N + n];
+    rho += f;
+    for (int d = 0; d < 3; ++d) j[d] += c[d] * f;
+    rhoE += in[((M + 1) * Q + i) * N + n];
+  }
+  double usp[3];
+  if (!p.weak) {
+    double o = 0.0;
+    for (int a = 0; a < M; ++a) if (a != p.slaved) o += ra[a];
+    ra[p.slaved] = rho - o;                                     // Eq. (rhoMATCH)
+    for (int d = 0; d < 3; ++d) usp[d] = j[d] / rho;
+  } else {
+    double rs = 0.0;
+    for (int a = 0; a < M; ++a) rs += ra[a];
+    for (int d = 0; d < 3; ++d) usp[d] = jsp[d] / rs;          // Eq. (uSPEC)
+  }
+  store_rec<M>(eq_rec_buf(side, N, p.rec_w, buf), n, p.rec_w, p.weak, eq_record64<M>(p, ra, rho, j, rhoE, usp));
+}
+
 // Replaces the state by natural-layout full populations (no terms pending).
+// With 16-bit storage the senders' records must be in place (rec_from_pops_kernel)
+// and no deferred terms pending.
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
-set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const double* __restrict__ base,
-                int parity, const double* __restrict__ in) {
+set_pops_kernel(const DevParams<Real> p, Store* __restrict__ pops, const Real* __restrict__ side,
+                const double* __restrict__ base, int parity, const double* __restrict__ in) {
   const long long n = gtid();
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  static_for<0, Q>([&](auto I_) {
+    constexpr int i = decltype(I_)::value;
     long long node; int slot;
     aa_read_loc<true>(parity, nb, n, i, node, slot);
+    Real sh[M + 2];
+#pragma unroll
+    for (int L = 0; L < M + 2; ++L) sh[L] = Real(0);
+    if constexpr (kEqCodec<Store, Real>) {
+      Real cf, cg;
+      eq_incoming<M, i, true>(p, side, nb, n, parity, cf, cg, sh);
+    }
     for (int L = 0; L < M + 2; ++L)
-      codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L, (Real)(in[(L * Q + i) * N + n] - base[L * Q + i]));
-  }
+      codec_store<Store, Real>(p, pops, (L * Q + slot) * N + node, L,
+                               (Real)((in[(L * Q + i) * N + n] - base[L * Q + i]) - (double)sh[L]));
+  });
 }
 
 // Training pairs of the learned closure at every node: the network's

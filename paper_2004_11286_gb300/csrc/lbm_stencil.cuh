@@ -16,6 +16,7 @@
 #pragma once
 
 #include "lbm_helpers.cuh"
+#include "lbm_eqcodec.cuh"
 
 namespace lbm {
 
@@ -55,11 +56,12 @@ __device__ __forceinline__ Real side_ld(const Real* p) {
 #endif
 }
 
+// The deferred terms of the population that `sender` sent in direction I,
+// for a sender whose theta is th.
 template <class Real, int I>
-__device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, long long N, long long sender,
-                                              Real& cf, Real& cg) {
+__device__ __forceinline__ void incoming_corr_th(const Real* __restrict__ side, long long N, long long sender,
+                                                 Real th, Real& cf, Real& cg) {
   constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
-  const Real th = side_ld(side + SP_THR * N + sender);
   Real kc = Real(0);
   if constexpr (cx != 0) kc += (cx > 0 ? side_ld(side + (SP_K + 0) * N + sender) : -side_ld(side + (SP_K + 0) * N + sender));
   if constexpr (cy != 0) kc += (cy > 0 ? side_ld(side + (SP_K + 1) * N + sender) : -side_ld(side + (SP_K + 1) * N + sender));
@@ -72,6 +74,39 @@ __device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, lon
     constexpr int a = cx ? 0 : (cy ? 1 : 2);
     constexpr int sg = cx + cy + cz;
     cf = (sg > 0 ? Real(0.5) : Real(-0.5)) * side_ld(side + (SP_X + a) * N + sender);
+  }
+}
+template <class Real, int I>
+__device__ __forceinline__ void incoming_corr(const Real* __restrict__ side, long long N, long long sender,
+                                              Real& cf, Real& cg) {
+  incoming_corr_th<Real, I>(side, N, sender, side_ld(side + SP_THR * N + sender), cf, cg);
+}
+
+// Reduced-precision storage: the record of the node that sent the population
+// arriving at n in direction I, the equilibrium shifts of every lattice for
+// that population (lbm_eqcodec.cuh) and its deferred terms.  The sender is
+// n - c_I; with walls, a population arriving from beyond a wall is n's own
+// population of direction opp(I) reflected, so it was stored with n's shift
+// for opp(I) and carries n's terms for I negated.
+template <int M, int I, bool WALL>
+__device__ __forceinline__ void eq_incoming(const DevParams<float>& p, const float* __restrict__ side,
+                                            const Nbr& nb, long long n, int parity, float& cf, float& cg,
+                                            float (&sh)[M + 2]) {
+  const long long N = p.N;
+  const float* rin = eq_rec_buf(side, N, p.rec_w, 1 - parity);
+  bool refl = false;
+  long long snd = n;
+  if constexpr (I != 13) {
+    if (WALL && arrives_from_wall(nb, I)) refl = true;
+    else snd = nb.idx(-cx_of(I), -cy_of(I), -cz_of(I));
+  }
+  const EqRec<M> r = load_rec<M>(rin, snd, p.rec_w, p.weak);
+  if (WALL && refl) eq_shift<M, opp_of(I)>(p, r, sh);
+  else eq_shift<M, I>(p, r, sh);
+  cf = 0.0f; cg = 0.0f;
+  if constexpr (I != 13) {
+    incoming_corr_th<float, I>(side, N, snd, p.thr + r.dth, cf, cg);
+    if (WALL && refl) { cf = -cf; cg = -cg; }
   }
 }
 
@@ -93,6 +128,24 @@ __device__ __forceinline__ void deferred_terms(const Real* __restrict__ side, lo
   incoming_corr<Real, I>(side, N, nb.idx(-cx_of(I), -cy_of(I), -cz_of(I)), cf, cg);
 }
 
+// The decoding terms of the population arriving at n in direction I for the
+// readers of the state: the deferred non-local terms cf (f) and cg (g), and
+// with 16-bit storage the equilibrium shifts sh of every lattice (zero
+// otherwise); walls are handled whether or not the grid has them.
+template <int M, class Real, class Store, int I>
+__device__ __forceinline__ void incoming_terms(const DevParams<Real>& p, const Real* __restrict__ side,
+                                               const Nbr& nb, long long n, int parity, Real& cf, Real& cg,
+                                               Real (&sh)[M + 2]) {
+  cf = Real(0); cg = Real(0);
+  if constexpr (kEqCodec<Store, Real>) {
+    eq_incoming<M, I, true>(p, side, nb, n, parity, cf, cg, sh);
+  } else {
+#pragma unroll
+    for (int L = 0; L < M + 2; ++L) sh[L] = Real(0);
+    if constexpr (I != 13) deferred_terms<Real, I, true>(side, p.N, nb, n, cf, cg);
+  }
+}
+
 // Zeroth/first moments of the (corrected) deviations needed by the
 // thermodynamic state (Eqs. densitya, auxua, f0momDensity, f1momMomentum,
 // g0momTotalEnergy).
@@ -110,22 +163,22 @@ __device__ __forceinline__ void load_state_moments(const DevParams<Real>& p, con
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     long long node; int slot;
     aa_read_loc<true>(parity, nb, n, i, node, slot);
-    Real cf = Real(0), cg = Real(0);
-    if constexpr (i != 13) deferred_terms<Real, i, true>(side, N, nb, n, cf, cg);
+    Real cf, cg, sh[M + 2];
+    incoming_terms<M, Real, Store, i>(p, side, nb, n, parity, cf, cg, sh);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+      const Real v = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a) + sh[a];
       rdev[a] += v;
       if (cx) ja[a][0] += cx * v;
       if (cy) ja[a][1] += cy * v;
       if (cz) ja[a][2] += cz * v;
     }
-    const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
+    const Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf + sh[M];
     rho_dev += fv;
     if (cx) j[0] += cx * fv;
     if (cy) j[1] += cy * fv;
     if (cz) j[2] += cz * fv;
-    rhoE_dev += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+    rhoE_dev += codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg + sh[M + 1];
   });
 }
 

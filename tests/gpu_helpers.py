@@ -26,10 +26,33 @@ def rel(a, b, floor=0.0):
 
 
 def field_errors(gm, om, cs):
-    """Relative errors per observable.  Velocity is floored at 1e-2 c_s: u =
-    j / rho is the small difference of populations of size rho w_i, so its
-    attainable relative accuracy degrades as c_s / |u|.  Mole fractions are
-    compared absolutely."""
+    """Relative errors per observable, max |a - b| / max(||b||_inf, floor):
+    rho, T, P unfloored; velocity floored at 1e-3 c_s (u = j / rho is the
+    small difference of populations of size rho w_i, so where the fluid is
+    nearly at rest its attainable relative accuracy degrades as c_s / |u|);
+    mole fractions absolutely (X_a ~ 0 in places)."""
     return dict(rho=rel(gm["rho"], om["rho"]), T=rel(gm["T"], om["T"]), P=rel(gm["P"], om["P"]),
-                u=rel(gm["u"], om["u"], floor=1e-2 * cs),
+                u=rel(gm["u"], om["u"], floor=1e-3 * cs),
                 X=float(np.abs(gm["X"] - om["X"]).max()))
+
+
+def deviation_errors(gm, om, min_signal=1e-4):
+    """Errors of the fields' deviations from their domain means, relative to
+    the oracle's deviation: max |(a - mean a) - (b - mean b)| / max |b - mean b|,
+    for rho, T, P and each X_a whose oracle deviation is live (at least
+    ``min_signal`` of the field's magnitude); the plain relative error of a
+    field that varies by 1e-4 can hide an error as large as its variation."""
+    out = {}
+    for k in ("rho", "T", "P"):
+        a, b = np.asarray(gm[k]), np.asarray(om[k])
+        db = b - b.mean()
+        den = float(np.abs(db).max())
+        if den >= min_signal * float(np.abs(b).max()):
+            out[k] = float(np.abs((a - a.mean()) - db).max() / den)
+    Xa, Xb = np.asarray(gm["X"]), np.asarray(om["X"])
+    for s in range(Xb.shape[0]):
+        db = Xb[s] - Xb[s].mean()
+        den = float(np.abs(db).max())
+        if den >= min_signal:
+            out[f"X{s}"] = float(np.abs((Xa[s] - Xa[s].mean()) - db).max() / den)
+    return out

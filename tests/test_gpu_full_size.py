@@ -91,10 +91,9 @@ def test_shear_layer_full_size_sampled_step_and_conservation():
 
 
 # The bands' 49-fold composition contrast (a 14-fold density contrast at
-# uniform pressure) makes the stored deviations O(f): FP32 arithmetic then
-# reaches ~1.1e-5 on u after 20 steps (held to 3e-5, as the ternary tube), and
-# BF16's 8 mantissa bits ~2 % on the temperature after 30.
-@pytest.mark.parametrize("precision,tol", [("fp32", 3e-5), ("bf16", 5e-2)])
+# uniform pressure): FP32 reaches 9.5e-6 (u) after 20 steps; BF16 storage of
+# the non-equilibrium parts 9.5e-5 (T).  Both within the contract.
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 1e-3), ("fp16", 1e-3)])
 def test_shear_layer_reduced_20_steps(precision, tol):
     wl = W.shear_layer(shape=(16, 64, 16), steps=20)
     prm = oracle_params(wl)

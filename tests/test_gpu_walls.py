@@ -53,6 +53,30 @@ def test_walled_random_state_steps(M, coupling, shape, precision):
     h.close()
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape", [(5, 7, 13), (4, 5, 8)])
+def test_walled_reduced_precision_steps(shape, precision):
+    """16-bit storage with walls: a population reflected at a wall was stored
+    against the node's own equilibrium for the opposite direction, and is
+    decoded with it (both parities).  A smooth ternary state at rest with
+    0.2 % population noise; every field within 1e-3, u with the floor of
+    the other 16-bit tests (BF16 holds the interdiffusion drift to a few
+    1e-3 of the 1e-3 c_s floor)."""
+    wl = W.random_mixture(M=3, shape=shape, seed=303)
+    prm = oracle_params(wl, walls_x=True)
+    pops = O.init_populations(wl.X, wl.u, wl.T, wl.P, prm) * W.perturbation((5, 27) + shape, 0.002, 3)
+    h = gpu_handle(wl, precision, walls_x=True)
+    h.set_populations(pops)
+    ref = pops
+    for k in range(4):
+        ref = O.step(ref, prm)
+        h.step(1)
+        errs = field_errors(h.moments_dict(), _moments(ref, prm), _cs(wl))
+        assert max(v for f, v in errs.items() if f != "u") < 1e-3, (k, errs)
+        assert errs["u"] < (1e-3 if precision == "fp16" else 6e-3), (k, errs)
+    h.close()
+
+
 def test_walls_change_the_result():
     # the same state on the periodic grid differs: the walls are in effect
     wl = W.random_mixture(M=3, shape=(4, 5, 8), seed=303, velocity=0.03)
