@@ -182,6 +182,38 @@ LBM_API lbm_status lbm_mix_diagnostics(lbm_mix_t h, double* sums);
 /* Waits for the handle's stream; reports latched device errors. */
 LBM_API lbm_status lbm_mix_synchronize(lbm_mix_t h);
 
+/* Fixes the reference rest state (mass fractions Y[M], normalised here,
+ * temperature T > 0, density rho > 0) that every population is stored
+ * relative to; init_fields then keeps it instead of deriving one from the
+ * fields' means.  Handles whose states are exchanged (z slabs) must share
+ * one reference.  The stored state, if any, is invalidated (init again). */
+LBM_API lbm_status lbm_mix_set_reference(lbm_mix_t h, const double* Y, double T, double rho);
+
+/* z-slab decomposition of a periodic (or x-walled) grid.  A slab is a handle
+ * whose grid is its nz_local planes of the global grid plus `ghost` planes
+ * below and above (nz = nz_local + 2 ghost, nz >= 3 ghost), periodic in z
+ * within itself.  After every step, each ghost region is refreshed with the
+ * `ghost` planes of the neighbouring slab that it mirrors: every population
+ * slot (the in-place layout of the current parity), every side field and,
+ * with 16-bit storage, both equilibrium-record buffers.  One step reads
+ * across at most three planes (the collision's neighbours, then the two
+ * stencil passes of the non-local terms of Eq. Xalpha), so with ghost >= 3
+ * the interior evolves exactly as the same planes of the undivided grid.
+ *   lbm_mix_halo_bytes:  bytes of one face's buffer;
+ *   lbm_mix_halo_pack:   copies the `ghost` interior planes next to face
+ *                        0 (-z: planes ghost..2 ghost-1) or 1 (+z: planes
+ *                        nz-2 ghost..nz-ghost-1) into the device buffer;
+ *   lbm_mix_halo_unpack: copies a buffer into the ghost planes of face 0
+ *                        (0..ghost-1) or 1 (nz-ghost..nz-1).
+ * Slab k's face-1 pack fills slab k+1's face 0, and its face-0 pack slab
+ * k-1's face 1 (slab indices periodic).  The buffer is caller-owned device
+ * memory, on this device or reachable from it (another GPU's buffer through
+ * peer access, or a receive buffer of a collective); ordered on the handle's
+ * stream.  LBM_ERR_ARG for a bad face, ghost or grid. */
+LBM_API lbm_status lbm_mix_halo_bytes(lbm_mix_t h, int ghost, size_t* bytes);
+LBM_API lbm_status lbm_mix_halo_pack(lbm_mix_t h, int face, int ghost, void* buf);
+LBM_API lbm_status lbm_mix_halo_unpack(lbm_mix_t h, int face, int ghost, const void* buf);
+
 /* Time steps taken since the last init_fields. */
 LBM_API long long lbm_mix_step_count(lbm_mix_t h);
 

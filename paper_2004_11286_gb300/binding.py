@@ -55,6 +55,10 @@ SIGNATURES = {
     "lbm_mix_set_populations": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
     "lbm_mix_diagnostics": (ct.c_int, [ct.c_void_p, _DP]),
     "lbm_mix_synchronize": (ct.c_int, [ct.c_void_p]),
+    "lbm_mix_set_reference": (ct.c_int, [ct.c_void_p, _DP, ct.c_double, ct.c_double]),
+    "lbm_mix_halo_bytes": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_size_t)]),
+    "lbm_mix_halo_pack": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]),
+    "lbm_mix_halo_unpack": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]),
     "lbm_mix_step_count": (ct.c_longlong, [ct.c_void_p]),
     "lbm_mix_launch_count": (ct.c_longlong, [ct.c_void_p]),
     "lbm_mix_enable_kernel_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
@@ -268,6 +272,27 @@ class LbmMix:
 
     def synchronize(self):
         self._check(self.lib.lbm_mix_synchronize(self.h))
+
+    def set_reference(self, Y, T: float, rho: float):
+        """Fix the reference rest state (mass fractions Y, temperature, density)."""
+        y = np.ascontiguousarray(np.asarray(Y, dtype=np.float64))
+        if y.size != self.M:
+            raise ValueError("Y must have M entries")
+        self._check(self.lib.lbm_mix_set_reference(self.h, y.ctypes.data_as(_DP), float(T), float(rho)))
+
+    def halo_bytes(self, ghost: int) -> int:
+        b = ct.c_size_t()
+        self._check(self.lib.lbm_mix_halo_bytes(self.h, int(ghost), ct.byref(b)))
+        return int(b.value)
+
+    def halo_pack(self, face: int, ghost: int, buf):
+        """Copy the `ghost` interior planes next to z face `face` into the
+        device tensor `buf` (uint8, halo_bytes(ghost) bytes)."""
+        self._check(self.lib.lbm_mix_halo_pack(self.h, int(face), int(ghost), ct.c_void_p(buf.data_ptr())))
+
+    def halo_unpack(self, face: int, ghost: int, buf):
+        """Copy the device tensor `buf` into the ghost planes of z face `face`."""
+        self._check(self.lib.lbm_mix_halo_unpack(self.h, int(face), int(ghost), ct.c_void_p(buf.data_ptr())))
 
     KERNEL_NAMES = ("collide_stream", "grad_GK", "grad_X")
 

@@ -139,6 +139,33 @@ red_final_kernel(const double* __restrict__ partials, int nblocks, int nv, doubl
   }
 }
 
+// z-face halo of a slab: `nfields` fields of `stride` elements each, of which
+// the `seg` elements from offset `off` are copied to (pack) or from (unpack)
+// the contiguous buffer.
+template <class T>
+__global__ void __launch_bounds__(256)
+halo_copy_kernel(T* __restrict__ state, T* __restrict__ buf, long long nfields, long long stride, long long off,
+                 long long seg, int unpack) {
+  const long long total = nfields * seg;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long f = k / seg, e = k - f * seg;
+    T* s = state + f * stride + off + e;
+    if (unpack) *s = buf[k]; else buf[k] = *s;
+  }
+}
+
+template <class T>
+cudaError_t halo_copy(void* state, void* buf, long long nfields, long long stride, long long off, long long seg,
+                      int unpack, cudaStream_t stream) {
+  const long long total = nfields * seg;
+  if (total <= 0) return cudaSuccess;
+  const long long want = (total + 255) / 256;
+  const unsigned grid = (unsigned)(want < 65536 ? want : 65536);
+  halo_copy_kernel<T><<<grid, 256, 0, stream>>>((T*)state, (T*)buf, nfields, stride, off, seg, unpack);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // Message reported by lbm_mix_last_error(NULL) for calls without a handle.
@@ -154,6 +181,7 @@ struct lbm_mix {
   double base[(lbm::MAXM + 2) * 27] = {};   // host copy of the reference rest equilibria
   double* d_base = nullptr;
   bool has_reference = false;
+  bool fixed_reference = false;    // set by lbm_mix_set_reference: init_fields keeps it
   void* pops = nullptr;
   size_t pops_bytes = 0;
   void* scratch = nullptr;
@@ -731,7 +759,7 @@ lbm_status lbm_mix_init_fields(lbm_mix_t h, const double* X, const double* u, co
     dX = st; du = st + M * N; dT = st + (M + 3) * N; dP = st + (M + 4) * N;
   }
   if ((s = h->cuda(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream), "clear flag")) != LBM_OK) return s;
-  if ((s = h->reference_from_fields(dX, dT, dP)) != LBM_OK) return s;
+  if (!h->fixed_reference && (s = h->reference_from_fields(dX, dT, dP)) != LBM_OK) return s;
   if ((s = h->clear_pending()) != LBM_OK) return s;
   if ((s = h->cuda(h->ks->init(h->ctx(), dX, du, dT, dP), "init kernel")) != LBM_OK) return s;
   h->launches += h->ks->setup_launches;
@@ -846,6 +874,81 @@ lbm_status lbm_mix_diagnostics(lbm_mix_t h, double* sums) {
   sums[h->M] += Nd * h->p64.RL[h->M];
   sums[h->M + 4] += Nd * h->p64.RL[h->M + 1];
   return s;
+}
+
+lbm_status lbm_mix_set_reference(lbm_mix_t h, const double* Y, double T, double rho) {
+  if (!h) return LBM_ERR_ARG;
+  if (!Y) return h->fail(LBM_ERR_ARG, "NULL mass fractions");
+  double Yn[lbm::MAXM], sum = 0.0;
+  for (int a = 0; a < h->M; ++a) {
+    if (!(Y[a] >= 0.0) || !std::isfinite(Y[a])) return h->fail(LBM_ERR_ARG, "mass fractions must be >= 0");
+    sum += Y[a];
+  }
+  if (!(sum > 0.0)) return h->fail(LBM_ERR_ARG, "mass fractions sum to zero");
+  for (int a = 0; a < h->M; ++a) Yn[a] = Y[a] / sum;
+  lbm_status s = h->set_reference(Yn, T, rho);
+  if (s != LBM_OK) return s;
+  h->fixed_reference = true;
+  h->initialized = false;      // a stored state was relative to the previous reference
+  return LBM_OK;
+}
+
+// The halo of a z slab: every population slot, side field and (16-bit
+// storage) equilibrium record of `ghost` planes.
+static lbm_status halo_check(lbm_mix_t h, int face, int ghost) {
+  if (face != 0 && face != 1) return h->fail(LBM_ERR_ARG, "face must be 0 (-z) or 1 (+z)");
+  if (ghost < 1) return h->fail(LBM_ERR_ARG, "ghost must be >= 1");
+  if ((long long)h->p64.nz < 3LL * ghost) return h->fail(LBM_ERR_ARG, "nz must be at least 3 * ghost");
+  return h->ready();
+}
+
+lbm_status lbm_mix_halo_bytes(lbm_mix_t h, int ghost, size_t* bytes) {
+  if (!h || !bytes) return LBM_ERR_ARG;
+  if (ghost < 1) return h->fail(LBM_ERR_ARG, "ghost must be >= 1");
+  const size_t plane = (size_t)h->p64.nx * (size_t)h->p64.ny;
+  *bytes = (size_t)ghost * plane * ((size_t)(h->M + 2) * 27 * store_elem_bytes(h->prec) +
+                                    (size_t)lbm::NSIDE * side_elem_bytes(h->prec) + 2 * (size_t)h->p64.rec_w * 4);
+  return LBM_OK;
+}
+
+static lbm_status halo_move(lbm_mix_t h, int face, int ghost, void* buf, int unpack) {
+  lbm_status s = halo_check(h, face, ghost);
+  if (s != LBM_OK) return s;
+  if (!buf) return h->fail(LBM_ERR_ARG, "NULL buffer");
+  const long long plane = (long long)h->p64.nx * h->p64.ny, nz = h->p64.nz, N = h->N;
+  // pack: the `ghost` interior planes next to the face; unpack: the ghost planes of the face
+  const long long z0 = unpack ? (face == 0 ? 0 : nz - ghost) : (face == 0 ? ghost : nz - 2LL * ghost);
+  const long long seg = (long long)ghost * plane;
+  const size_t es = store_elem_bytes(h->prec), ss = side_elem_bytes(h->prec);
+  const long long nf = (long long)(h->M + 2) * 27;
+  char* b = (char*)buf;
+  cudaError_t e;
+  if (es == 8) e = halo_copy<double>(h->pops, b, nf, N, z0 * plane, seg, unpack, h->stream);
+  else if (es == 4) e = halo_copy<float>(h->pops, b, nf, N, z0 * plane, seg, unpack, h->stream);
+  else e = halo_copy<unsigned short>(h->pops, b, nf, N, z0 * plane, seg, unpack, h->stream);
+  b += (size_t)nf * seg * es;
+  if (e == cudaSuccess) {
+    if (ss == 8) e = halo_copy<double>(h->scratch, b, lbm::NSIDE, N, z0 * plane, seg, unpack, h->stream);
+    else e = halo_copy<float>(h->scratch, b, lbm::NSIDE, N, z0 * plane, seg, unpack, h->stream);
+  }
+  b += (size_t)lbm::NSIDE * seg * ss;
+  const long long rw = h->p64.rec_w;
+  if (e == cudaSuccess && rw > 0)
+    e = halo_copy<float>((float*)h->scratch + lbm::eq_rec_offset(N), b, 2, rw * N, z0 * plane * rw, seg * rw, unpack,
+                         h->stream);
+  if ((s = h->cuda(e, unpack ? "halo unpack" : "halo pack")) != LBM_OK) return s;
+  h->launches += rw > 0 ? 3 : 2;
+  return LBM_OK;
+}
+
+lbm_status lbm_mix_halo_pack(lbm_mix_t h, int face, int ghost, void* buf) {
+  if (!h) return LBM_ERR_ARG;
+  return halo_move(h, face, ghost, buf, 0);
+}
+
+lbm_status lbm_mix_halo_unpack(lbm_mix_t h, int face, int ghost, const void* buf) {
+  if (!h) return LBM_ERR_ARG;
+  return halo_move(h, face, ghost, const_cast<void*>(buf), 1);
 }
 
 lbm_status lbm_mix_synchronize(lbm_mix_t h) {
