@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the secondary lines (eight-species mixture, ensemble) of the default run")
     ap.add_argument("--no-parity", action="store_true", help="skip the per-field errors against the oracle")
+    ap.add_argument("--decompose", action="store_true",
+                    help="under torchrun: one z slab of a (n*N) x n x n grid per rank, ghost planes exchanged "
+                         "point to point (NCCL) after every step, instead of independent replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["shear", "acoustic", "ensemble", "mixture"], default="shear",
@@ -456,6 +459,59 @@ def _bench_mixture(a, dev):
 
 
 # ---------------------------------------------------------------------------
+def _bench_decomposed(a, name, dev, rank, world):
+    """Weak scaling over a z-slab decomposition: the global grid is
+    (n * world) x n x n; rank r steps its n planes plus three ghost planes
+    per side and exchanges them with ranks r +- 1 after every step
+    (slabs.DistributedSlab, NCCL point to point).  Each rank draws its own
+    slab of the recipe (the shear layer varies along y only, so every slab
+    has the same mean state and reference)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2004_11286_gb300 import binding, workloads as W
+    from paper_2004_11286_gb300.slabs import GHOST, DistributedSlab, reference_state
+    n = a.n
+    ext = (n + 2 * GHOST, n, n)
+    wl = W.shear_layer(shape=ext, seed=1234 + rank) if name == "shear" else W.acoustic_pulse(shape=ext)
+    slaved = W.slaved_species(wl)
+
+    def make(shape, device):
+        return binding.LbmMix(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, shape=shape,
+                              precision=a.precision, slaved=slaved, R_U=wl.R_U, device=dev)
+
+    sl = DistributedSlab(make, (n * world, n, n), wl.molar_mass, wl.R_U)
+    sl.init_local(wl.X, wl.u, wl.T, wl.P, reference_state(wl.X, wl.T, wl.P, wl.molar_mass, wl.R_U))
+    sl.step(a.warmup)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(_physical_gpu_index(int(os.environ.get("LOCAL_RANK", "0")))) if rank == 0 else None
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(sl.h.stream)
+    sl.step(a.steps)
+    ev1.record(sl.h.stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    dist.barrier()
+    ms = _max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    clk = None
+    if clocks is not None:
+        clocks.mark(t0, t1)
+        clk = clocks.stop()
+    nodes = n ** 3
+    sl.close()
+    return {"metric": METRIC, "value": round(_job_mlups(world, nodes, a.steps, ms * 1e-3), 2), "unit": UNIT,
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if a.precision == "fp32" else a.precision, "data": "synthetic",
+            "config": {"workload": f"{name} recipe, z-slab decomposition of a {n * world}x{n}x{n} grid, {n}^3 "
+                                   f"interior planes per rank plus {GHOST} ghost planes per side exchanged by "
+                                   "NCCL point-to-point after every step", "parallelism": f"z slabs x{world}",
+                       "l2": "inputs larger than L2, no flush"},
+            "clocks": clk, "gpu_launches": int(a.steps * 3 + a.steps * (6 if a.precision in ("fp16", "bf16") else 4))}
+
+
 def _parity(name: str, dev):
     """Per-field errors against the FP64 oracle on a reduced copy of the
     workload (same recipe and constants, a grid the oracle steps in seconds),
@@ -570,6 +626,13 @@ def main():
         line = _bench_ensemble(a, dev) if a.workload == "ensemble" else _bench_mixture(a, dev)
         if rank == 0:
             print(json.dumps(line), flush=True)
+        return
+
+    if world > 1 and a.decompose:
+        line = _bench_decomposed(a, name, dev, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
         return
 
     wl = _workload(name, a.n)

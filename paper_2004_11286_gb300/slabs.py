@@ -226,6 +226,13 @@ class DistributedSlab:
         self.h.set_reference(Y, Tr, rho)
         self.h.init_fields(sl(X), sl(u), sl(T), sl(P))
 
+    def init_local(self, X, u, T, P, reference):
+        """This slab's own fields on its extended planes (ghosts included) and
+        the reference state (Y, T, rho) every rank uses."""
+        Y, Tr, rho = reference
+        self.h.set_reference(Y, Tr, rho)
+        self.h.init_fields(X, u, T, P)
+
     def exchange(self):
         dist = self._dist
 
@@ -238,7 +245,8 @@ class DistributedSlab:
 
         def transport(sends, recvs):
             if self.world == 1:
-                return [sends[1 - face][0] for face, _ in recvs]
+                # the bottom ghosts take this slab's own top planes (sends[0]), the top ghosts its bottom ones
+                return [sends[face][0] for face, _ in recvs]
             self.h.stream.synchronize()
             ops = [dist.P2POp(dist.isend, buf, dst) for buf, dst in sends]
             ops += [dist.P2POp(dist.irecv, self.inb[face], src) for face, src in recvs]

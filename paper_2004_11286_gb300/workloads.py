@@ -183,6 +183,93 @@ def shear_layer(n: int = 256, mach: float = 0.3, delta: float = 4.0, noise: floa
     return Workload("shear_layer", mm, cv, D, mu, lam, X, u, T, P, steps)
 
 
+# The closed-tube cases of Sec. 4.2 (Eqs. ternaryConditions,
+# ternaryConditionsCH4, ternaryConditionsH2): left / right mole fractions of
+# H2, Ar, CH4.
+LOSCHMIDT_CASES = {
+    "1T": ([0.491, 0.509, 0.000], [0.000, 0.485, 0.515]),
+    "2T": ([0.512, 0.000, 0.448], [0.000, 0.485, 0.515]),
+    "3T": ([0.512, 0.000, 0.448], [0.491, 0.509, 0.000]),
+}
+# Binary diffusivities the section prints (1e-5 m^2/s): H2-Ar, H2-CH4, Ar-CH4.
+LOSCHMIDT_D = (8.14543, 7.37433, 2.17321)
+
+
+def loschmidt_tube(case: str = "1T", L: int = 96, width: float = 3.0, floor: float = 0.01,
+                   D_h2_ar: float = 0.05, steps: int = 0) -> Workload:
+    """The ternary Loschmidt tube of Sec. 4.2 (H2/Ar/CH4, molar masses 2.016,
+    39.948, 16.043) on an L x 1 x 1 grid closed by walls at both x ends:
+    the case's left and right compositions joined by a tanh step of the given
+    width at the middle, every mole fraction floored at `floor` and the
+    sides renormalised (a trace species left at zero drives the method
+    unstable, as the design notes record).  The binary diffusivities keep
+    the printed ratios, scaled so that D(H2, Ar) = D_h2_ar in lattice units.
+    Uniform T and P, at rest."""
+    XL, XR = (np.maximum(floor, np.asarray(v, dtype=np.float64)) for v in LOSCHMIDT_CASES[case])
+    XL, XR = XL / XL.sum(), XR / XR.sum()
+    mm = np.array([2.016, 39.948, 16.043])
+    cv = np.array([2.5, 1.5, 3.0])
+    d12, d13, d23 = (v * D_h2_ar / LOSCHMIDT_D[0] for v in LOSCHMIDT_D)
+    D = np.array([[0.0, d12, d13], [d12, 0.0, d23], [d13, d23, 0.0]])
+    x = np.arange(L, dtype=np.float64)
+    s = 0.5 * (1.0 + np.tanh((x - (L / 2.0 - 0.5)) / width))
+    X = ((1.0 - s)[None] * XL[:, None] + s[None] * XR[:, None]).reshape(3, 1, 1, L)
+    T = np.full((1, 1, L), T_AMBIENT)
+    P0 = _p0(X.reshape(3, -1).mean(axis=1), mm, T_AMBIENT)
+    P = np.full((1, 1, L), P0)
+    mu, lam = _transport(mm, cv, P0, 0.1)
+    return Workload(f"loschmidt_{case}", mm, cv, D, mu, lam, X, np.zeros((3, 1, 1, L)), T, P, steps)
+
+
+def khi_n2_h2o(shape=(200, 800, 800), reynolds: float = 11963.46, mach_r: float = 0.2, schmidt: float = 0.6,
+               width: float = 0.0, steps: int = 0) -> Workload:
+    """The three-dimensional Kelvin-Helmholtz instability of Sec. 4.5
+    (Eqs. icKHI, uyKHI, uzKHI): N2 / H2O (molar masses 28.0134, 18.015;
+    diatomic, polyatomic) on a periodic Lz x Ly x Lx grid (default
+    200 x 800 x 800).  Three layers along y: X_H2O = 0.9 and u_x = +U for
+    y < Ly/4 and y >= 3 Ly/4, X_H2O = 0.1 and u_x = -U between, with
+    U = (mach_r / 2) c_s (relative Mach number mach_r, c_s of the 50/50
+    mixture); u_y = 2U 0.01 sin(2 pi x / Lx), u_z = 2U 0.01 sin(2 pi z / Lz).
+    The layers are sharp steps (width 0) or tanh steps of the given width.
+    The species viscosity gives Re = 2 U Ly / nu in the bottom layer
+    (nu = mu / rho, equal mu_a); the binary diffusivity D = nu / schmidt (the
+    paper gives none); conductivities for Pr = 0.71.  Uniform T and P."""
+    mm = np.array([28.0134, 18.015])
+    cv = np.array([2.5, 3.0])
+    nz, ny, nx = shape
+    y = np.arange(ny, dtype=np.float64)
+    if width > 0.0:
+        outer = 1.0 - 0.5 * (np.tanh((y - ny / 4.0) / width) - np.tanh((y - 3.0 * ny / 4.0) / width))
+    else:
+        outer = ((y < ny / 4.0) | (y >= 3.0 * ny / 4.0)).astype(np.float64)
+    xh2o = 0.1 + 0.8 * outer
+    X = np.empty((2, nz, ny, nx))
+    X[1] = xh2o[None, :, None]
+    X[0] = 1.0 - X[1]
+    m50 = 0.5 * (mm[0] + mm[1])
+    y50 = 0.5 * mm / m50
+    cv50 = float(np.dot(y50, cv / mm))
+    gamma50 = (cv50 + 1.0 / m50) / cv50
+    c50 = np.sqrt(gamma50 * T_AMBIENT / m50)
+    U = 0.5 * mach_r * c50
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = (U * (2.0 * outer - 1.0))[None, :, None]
+    x = np.arange(nx, dtype=np.float64)
+    z = np.arange(nz, dtype=np.float64)
+    u[1] = (2.0 * U * 0.01 * np.sin(2.0 * np.pi * x / nx))[None, None, :]
+    u[2] = (2.0 * U * 0.01 * np.sin(2.0 * np.pi * z / nz))[:, None, None]
+    T = np.full((nz, ny, nx), T_AMBIENT)
+    P0 = _p0(np.array([0.5, 0.5]), mm, T_AMBIENT)
+    P = np.full((nz, ny, nx), P0)
+    m_bottom = 0.1 * mm[0] + 0.9 * mm[1]
+    rho_bottom = P0 * m_bottom / T_AMBIENT
+    nu = 2.0 * U * ny / reynolds
+    mu = np.full(2, nu * rho_bottom)
+    lam = mu * (cv + 1.0) / mm / PR_TARGET
+    D = np.array([[0.0, nu / schmidt], [nu / schmidt, 0.0]])
+    return Workload("khi_n2_h2o", mm, cv, D, mu, lam, X, u, T, P, steps)
+
+
 def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
                    shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0,
                    field_seed: Optional[int] = None, amplitude: float = 0.5) -> Workload:

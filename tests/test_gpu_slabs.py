@@ -70,3 +70,37 @@ def test_halo_arguments_are_checked():
     h.halo_pack(0, 2, buf)
     h.halo_unpack(1, 2, buf)
     h.close()
+
+
+def test_distributed_slab_on_one_rank_wraps_onto_itself():
+    """DistributedSlab with a world of one rank: its two faces exchange with
+    each other (the periodic grid through its own ghost planes), which must
+    again reproduce one handle on the whole grid bit for bit."""
+    import os
+    import torch.distributed as dist
+    from paper_2004_11286_gb300 import binding
+    from paper_2004_11286_gb300.slabs import GHOST, DistributedSlab, extended_planes
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29517")
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        wl = W.random_mixture(M=3, shape=(10, 6, 8), seed=71, velocity=0.02)
+        Y, T, rho = reference_state(wl.X, wl.T, wl.P, wl.molar_mass, wl.R_U)
+
+        def make(shape, dev):
+            return binding.LbmMix(wl.molar_mass, wl.cv_molar, wl.D, mu=wl.mu, lam=wl.lam, shape=shape,
+                                  precision="fp32", slaved=W.slaved_species(wl), R_U=wl.R_U)
+
+        sl = DistributedSlab(make, wl.shape, wl.molar_mass, wl.R_U)
+        sl.init_fields(wl.X, wl.u, wl.T, wl.P)
+        one = gpu_handle(wl, "fp32")
+        one.set_reference(Y, T, rho)
+        one.init_fields(wl.X, wl.u, wl.T, wl.P)
+        sl.step(7)
+        one.step(7)
+        a = sl.h.populations()[:, :, GHOST:-GHOST]
+        assert np.array_equal(a, one.populations())
+        sl.close()
+        one.close()
+    finally:
+        dist.destroy_process_group()
