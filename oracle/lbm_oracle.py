@@ -86,6 +86,9 @@ class Params:
     coupling: str = "strong"
     slaved: int = -1
     walls_x: bool = False           # bounce-back walls at x = -1/2 and x = nx - 1/2
+    # temperature-dependent specific heats (Sec. 3.1): C-bar_{a,v}(T) / R_U =
+    # sum_k cv_poly[a, k] T^k; None: the constants cv_molar (T0 = 0 either way)
+    cv_poly: Optional[np.ndarray] = None
     M: int = field(init=False)
 
     def __post_init__(self):
@@ -108,6 +111,8 @@ class Params:
         if self.slaved < 0:
             self.slaved = self.M - 1
         assert self.coupling in ("strong", "weak")
+        if self.cv_poly is not None:
+            self.cv_poly = np.asarray(self.cv_poly, dtype=np.float64).reshape(self.M, -1)
 
     @property
     def S(self) -> int:
@@ -127,6 +132,36 @@ class Params:
     def Cp_a(self) -> np.ndarray:
         """Mayer's relation in the mass basis, C_{a,p} - C_{a,v} = R_a (Sec. 3.1)."""
         return self.Cv_a + self.R_a
+
+    def _coef(self) -> np.ndarray:
+        """(M, K) coefficients of C-bar_{a,v}(T) / R_U in powers of T."""
+        return self.cv_poly if self.cv_poly is not None else self.cv_molar[:, None]
+
+    def cv_a_of(self, T) -> np.ndarray:
+        """C_{a,v}(T) = C-bar_{a,v}(T) / m_a per species, shape (M,) + T.shape."""
+        T = np.asarray(T, dtype=np.float64)
+        c = self._coef()
+        out = np.zeros((self.M,) + T.shape)
+        for k in range(c.shape[1]):
+            out = out + (c[:, k] * self.R_U / self.molar_mass).reshape((self.M,) + (1,) * T.ndim) * T[None] ** k
+        return out
+
+    def U_a_of(self, T) -> np.ndarray:
+        """Eq. (specUa) with T0 = 0: U_a(T) = int_0^T C_{a,v}(T') dT', the
+        polynomial's integral term by term."""
+        T = np.asarray(T, dtype=np.float64)
+        c = self._coef()
+        out = np.zeros((self.M,) + T.shape)
+        for k in range(c.shape[1]):
+            out = out + (c[:, k] * self.R_U / self.molar_mass / (k + 1)).reshape((self.M,) + (1,) * T.ndim) \
+                * T[None] ** (k + 1)
+        return out
+
+    def H_a_of(self, T) -> np.ndarray:
+        """Eq. (specHa) with T0 = 0: H_a(T) = int_0^T C_{a,p} dT' = U_a(T) + R_a T
+        (Mayer's relation in the mass basis)."""
+        T = np.asarray(T, dtype=np.float64)
+        return self.U_a_of(T) + self.R_a.reshape((self.M,) + (1,) * T.ndim) * T[None]
 
 
 # ----------------------------------------------------------------------------
@@ -286,10 +321,15 @@ def node_state(mom, prm: Params):
     m = 1.0 / inv_m
     X = Y * (m[None] / prm.molar_mass.reshape((M,) + (1,) * m.ndim))  # Eq. (moleFractionDefinition)
     R = prm.R_U / m                                             # Eq. (defineSpecificGasContant)
-    Cv = np.einsum("a...,a->...", Y, prm.Cv_a)                 # Eq. (Cvmix)
-    Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
     usq = (u * u).sum(axis=0)
-    T = (mom["rhoE"] / rho - 0.5 * usq) / Cv                    # Eq. (temperature2), T0 = 0
+    if prm.cv_poly is None:
+        Cv = np.einsum("a...,a->...", Y, prm.Cv_a)             # Eq. (Cvmix)
+        Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
+        T = (mom["rhoE"] / rho - 0.5 * usq) / Cv                # Eq. (temperature2), T0 = 0
+    else:
+        T = temperature_from_energy(Y, mom["rhoE"] / rho - 0.5 * usq, prm)   # Eq. (temperature)
+        Cv = np.einsum("a...,a...->...", Y, prm.cv_a_of(T))
+        Cp = Cv + R
     P = rho * R * T                                             # Eq. (eosIdealGas)
     st.update(rho_a=rho_a, j_a=j_a, rho_sp=rho_sp, u_sp=u_sp, u=u, Y=Y, m=m, X=X,
               R=R, Cv=Cv, Cp=Cp, T=T, P=P, usq=usq)
@@ -322,6 +362,24 @@ def node_state(mom, prm: Params):
         omega1 = 2.0 * P * Cp / (P * Cp + 2.0 * lam_mix)        # Eq. (omega1), dt = 1
     st.update(omega=omega, omega1=omega1)
     return st
+
+
+def temperature_from_energy(Y, e, prm: Params, tol: float = 1e-15, maxit: int = 60):
+    """Eq. (temperature) with T0 = 0: the T that solves
+    sum_a Y_a U_a(T) = e  (e = E - u^2/2), by Newton's method from the
+    estimate of the specific heats at T = 0.  U is increasing (C_v > 0), so
+    the iteration converges; it stops when the correction is below tol of T."""
+    e = np.asarray(e, dtype=np.float64)
+    cv0 = np.einsum("a...,a...->...", Y, prm.cv_a_of(np.zeros_like(e)))
+    T = e / cv0
+    for _ in range(maxit):
+        U = np.einsum("a...,a...->...", Y, prm.U_a_of(T))
+        Cv = np.einsum("a...,a...->...", Y, prm.cv_a_of(T))
+        dT = (U - e) / Cv
+        T = T - dT
+        if np.all(np.abs(dT) <= tol * np.abs(T)):
+            break
+    return T
 
 
 def inv_tau_ab(st, prm: Params):
@@ -420,8 +478,8 @@ def collide(pops, prm: Params, return_aux: bool = False):
     # --- energy lattice, Eqs. (g), (geq1mom), (geq2mom), (gstareq1mom) -------
     g = pops[M + 1]
     theta = R * T
-    H_a = np.stack([prm.Cp_a[a] * T for a in range(M)])       # Eq. (specHa), T0 = 0
-    H = st["Cp"] * T                                           # Eq. (specH)
+    H_a = prm.H_a_of(T)                                        # Eq. (specHa), T0 = 0
+    H = np.einsum("a...,a...->...", st["Y"], H_a)             # Eq. (specH)
     eye = np.eye(3)
     Peq = np.empty((3, 3) + rho.shape)
     for a in range(3):
@@ -503,15 +561,14 @@ def init_populations(X, u, T, P, prm: Params):
     rho = P / (R * T)
     rho_a = Y * rho[None]
     j = rho[None] * u
-    Cv = np.einsum("a...,a->...", Y, prm.Cv_a)
-    Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
     usq = (u * u).sum(axis=0)
-    rhoE = rho * (Cv * T + 0.5 * usq)
+    Ua = prm.U_a_of(T)
+    rhoE = rho * (np.einsum("a...,a...->...", Y, Ua) + 0.5 * usq)   # rho (U + u^2/2), Eq. (Umix)
     pops = np.empty((M + 2, Q) + T.shape)
     for a in range(M):
         pops[a] = rho_a[a] * psi_product(u, prm.R_a[a] * T)
     pops[M] = rho * psi_product(u, R * T)
-    H = Cp * T
+    H = np.einsum("a...,a...->...", Y, prm.H_a_of(T))        # Eq. (specH)
     hk = H + 0.5 * usq
     eye = np.eye(3)
     Peq = np.empty((3, 3) + T.shape)
