@@ -478,8 +478,12 @@ def collide(pops, prm: Params, return_aux: bool = False):
     # --- energy lattice, Eqs. (g), (geq1mom), (geq2mom), (gstareq1mom) -------
     g = pops[M + 1]
     theta = R * T
-    H_a = prm.H_a_of(T)                                        # Eq. (specHa), T0 = 0
-    H = np.einsum("a...,a...->...", st["Y"], H_a)             # Eq. (specH)
+    if prm.cv_poly is None:
+        H_a = np.stack([prm.Cp_a[a] * T for a in range(M)])   # Eq. (specHa), constant heats, T0 = 0
+        H = st["Cp"] * T                                       # Eq. (specH)
+    else:
+        H_a = prm.H_a_of(T)                                    # Eq. (specHa), T0 = 0
+        H = np.einsum("a...,a...->...", st["Y"], H_a)         # Eq. (specH)
     eye = np.eye(3)
     Peq = np.empty((3, 3) + rho.shape)
     for a in range(3):
@@ -562,13 +566,18 @@ def init_populations(X, u, T, P, prm: Params):
     rho_a = Y * rho[None]
     j = rho[None] * u
     usq = (u * u).sum(axis=0)
-    Ua = prm.U_a_of(T)
-    rhoE = rho * (np.einsum("a...,a...->...", Y, Ua) + 0.5 * usq)   # rho (U + u^2/2), Eq. (Umix)
+    if prm.cv_poly is None:
+        Cv = np.einsum("a...,a->...", Y, prm.Cv_a)
+        Cp = np.einsum("a...,a->...", Y, prm.Cp_a)
+        rhoE = rho * (Cv * T + 0.5 * usq)
+        H = Cp * T
+    else:
+        rhoE = rho * (np.einsum("a...,a...->...", Y, prm.U_a_of(T)) + 0.5 * usq)   # rho (U + u^2/2), Eq. (Umix)
+        H = np.einsum("a...,a...->...", Y, prm.H_a_of(T))                          # Eq. (specH)
     pops = np.empty((M + 2, Q) + T.shape)
     for a in range(M):
         pops[a] = rho_a[a] * psi_product(u, prm.R_a[a] * T)
     pops[M] = rho * psi_product(u, R * T)
-    H = np.einsum("a...,a...->...", Y, prm.H_a_of(T))        # Eq. (specH)
     hk = H + 0.5 * usq
     eye = np.eye(3)
     Peq = np.empty((3, 3) + T.shape)
