@@ -79,7 +79,7 @@ enum { LBM_CLOSURE_EXACT = 0, LBM_CLOSURE_MLP = 1 };
 typedef struct {
   int M;                      /* number of species, 1..8 */
   const double* molar_mass;   /* [M] m_a > 0; R_a = R_U / m_a (Eq. Ra) */
-  const double* cv_molar;     /* [M] C-bar_{a,v} / R_U > 0 (Sec. 3.1, constant) */
+  const double* cv_molar;     /* [M] C-bar_{a,v} / R_U > 0 (Sec. 3.1, constant heats) */
   const double* D;            /* [M*M] row-major, symmetric binary diffusivities
                                  D_ab > 0 (Eq. smDiffusionCoefficients2).  A
                                  diagonal entry <= 0 selects the default
@@ -116,6 +116,15 @@ typedef struct {
   double closure_residual_bound; /* LBM_CLOSURE_MLP: largest accepted
                                  max_{a,c} |(A J~ - r/s)_{a,c}| of the J-form system
                                  in units of s = max|r| (<= 0 -> 1e-2) */
+  const double* cv_poly;      /* NULL: constant heats cv_molar.  Else [M][cv_terms]
+                                 row-major, temperature-dependent heats (Sec. 3.1):
+                                 C-bar_{a,v}(T) / R_U = sum_k cv_poly[a][k] T^k, T0 = 0;
+                                 U_a, H_a are their integrals (Eqs. specUa,
+                                 specHa) and T solves Eq. (temperature) per node.
+                                 C-bar_{a,v} must stay > 0 over the temperatures
+                                 reached.  FP64 and FP32 storage; not with walls,
+                                 LBM_CLOSURE_MLP or in a batch (LBM_ERR_UNSUPPORTED). */
+  int cv_terms;               /* 1..3 coefficients per species with cv_poly */
 } lbm_mix_params;
 
 typedef struct lbm_mix* lbm_mix_t;
@@ -127,10 +136,11 @@ typedef struct lbm_mix* lbm_mix_t;
 LBM_API lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t* out);
 
 /* Bytes the caller must provide for the populations (S*27*N elements of the
- * storage type) and the scratch side fields (17*N reals, FP64 in FP64 mode,
+ * storage type) and the scratch side fields (20*N reals, FP64 in FP64 mode,
  * FP32 otherwise: Phi_alpha, 1/omega-1/2, C_p, the q^corr scale and theta
  * written by each collision; G_alpha, K_alpha and the sender's theta; X_alpha
- * of Eq. Xalpha).  The scratch also carries the previous step's non-local
+ * of Eq. Xalpha; with temperature-dependent heats the mixture enthalpy's
+ * polynomial coefficients and T).  The scratch also carries the previous step's non-local
  * terms, which the next step applies to the arriving populations.  With
  * 16-bit storage the scratch holds, after the side fields (rounded up to 256
  * bytes), two buffers of per-node equilibrium records of

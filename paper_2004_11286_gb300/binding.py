@@ -38,6 +38,7 @@ class lbm_mix_params(ct.Structure):
         ("closure", ct.c_int),
         ("fp64_cond_bound", ct.c_double),
         ("closure_residual_bound", ct.c_double),
+        ("cv_poly", _DP), ("cv_terms", ct.c_int),
     ]
 
 
@@ -128,9 +129,10 @@ def _dp(a: Optional[np.ndarray]):
 def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), precision: str = "fp32",
                 coupling: str = "strong", slaved: int = -1, omega_fixed: float = 0.0, omega1_fixed: float = 0.0,
                 R_U: float = 1.0, fp64_cond_bound: float = 0.0, closure: str = "exact",
-                closure_bound: float = 0.0, walls_x: bool = False):
+                closure_bound: float = 0.0, walls_x: bool = False, cv_poly=None):
     """(lbm_mix_params, keepalive arrays) for one nz x ny x nx domain, periodic,
-    or with bounce-back walls on both x faces (walls_x)."""
+    or with bounce-back walls on both x faces (walls_x); cv_poly (M, K <= 3):
+    temperature-dependent molar heats C-bar_{a,v}(T)/R_U = sum_k cv_poly[a, k] T^k."""
     M = int(len(molar_mass))
     nz, ny, nx = (int(v) for v in shape)
     keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in (molar_mass, cv_molar, D)]
@@ -152,6 +154,14 @@ def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), pre
     p.closure = CLOSURE[closure]
     p.fp64_cond_bound = float(fp64_cond_bound)
     p.closure_residual_bound = float(closure_bound)
+    if cv_poly is not None:
+        cp = np.ascontiguousarray(np.asarray(cv_poly, dtype=np.float64).reshape(M, -1))
+        keep.append(cp)
+        p.cv_poly = _dp(cp)
+        p.cv_terms = int(cp.shape[1])
+    else:
+        p.cv_poly = _dp(None)
+        p.cv_terms = 0
     return p, keep
 
 
@@ -167,7 +177,7 @@ class LbmMix:
                  precision: str = "fp32", coupling: str = "strong", slaved: int = -1,
                  omega_fixed: float = 0.0, omega1_fixed: float = 0.0, R_U: float = 1.0,
                  fp64_cond_bound: float = 0.0, closure: str = "exact", closure_bound: float = 0.0,
-                 walls_x: bool = False, device=None, stream=None):
+                 walls_x: bool = False, device=None, stream=None, cv_poly=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -179,7 +189,8 @@ class LbmMix:
         p, self._keep = make_params(molar_mass, cv_molar, D, mu=mu, lam=lam, shape=shape, precision=precision,
                                     coupling=coupling, slaved=slaved, omega_fixed=omega_fixed,
                                     omega1_fixed=omega1_fixed, R_U=R_U, fp64_cond_bound=fp64_cond_bound,
-                                    closure=closure, closure_bound=closure_bound, walls_x=walls_x)
+                                    closure=closure, closure_bound=closure_bound, walls_x=walls_x,
+                                    cv_poly=cv_poly)
         self._owned = True
         self.precision = precision
         with torch.cuda.device(self.device):

@@ -65,6 +65,11 @@ void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   for (int L = 0; L < lbm::MAXM + 2; ++L)
     for (int k = 0; k < 4; ++k) d.bref[L][k] = (Real)s.bref[L][k];
   d.rec_w = s.rec_w;
+  d.tvar = s.tvar; d.nterm = s.nterm; d.Ur = (Real)s.Ur;
+  for (int a = 0; a < lbm::MAXM; ++a) {
+    d.Uar[a] = (Real)s.Uar[a];
+    for (int k = 0; k < 3; ++k) { d.cvp[a][k] = (Real)s.cvp[a][k]; d.Uc[a][k] = (Real)s.Uc[a][k]; d.Hc[a][k] = (Real)s.Hc[a][k]; }
+  }
   for (int a = 0; a < lbm::MAXM; ++a) d.Yr[a] = (Real)s.Yr[a];
   d.Tr = (Real)s.Tr; d.Rr = (Real)s.Rr; d.thr = (Real)s.thr; d.Pr = (Real)s.Pr; d.Cvr = (Real)s.Cvr;
   d.cE = (Real)s.cE; d.cPi = (Real)s.cPi; d.cS = (Real)s.cS; d.Rsp = (Real)s.Rsp;
@@ -277,13 +282,16 @@ struct lbm_mix {
     auto W = [&](int i, double z) {
       return w1(lbm::cx_of(i), z) * w1(lbm::cy_of(i), z) * w1(lbm::cz_of(i), z);
     };
-    double inv_m = 0.0, Cv = 0.0;
-    for (int a = 0; a < M; ++a) { inv_m += Y[a] * d.inv_mass[a]; Cv += Y[a] * d.Cv_a[a]; }
+    double inv_m = 0.0, Cv = 0.0, Umix = 0.0;
+    for (int a = 0; a < M; ++a) {
+      inv_m += Y[a] * d.inv_mass[a]; Cv += Y[a] * d.Cv_a[a];
+      Umix += Y[a] * lbm::U_a64(d, a, T);                    // Eqs. specUa, Umix
+    }
     const double R = d.R_U * inv_m, th = R * T;
     for (int a = 0; a < M; ++a)
       for (int i = 0; i < 27; ++i) base[a * 27 + i] = Y[a] * rho * W(i, d.R_a[a] * T);     // Eq. (27eq) at rest
     for (int i = 0; i < 27; ++i) base[M * 27 + i] = rho * W(i, th);                      // Eq. (feq) at rest
-    const double rhoE = rho * Cv * T, P = rho * th, Z = 0.5 * (1.0 - 3.0 * th) * P;
+    const double rhoE = rho * (d.tvar ? Umix : Cv * T), P = rho * th, Z = 0.5 * (1.0 - 3.0 * th) * P;
     for (int i = 0; i < 27; ++i) {                                                       // Eq. (gieq) at rest
       const int c2 = lbm::c2_of(i);
       const double E = rhoE - 1.5 * P + 0.5 * c2 * rho;
@@ -323,6 +331,16 @@ struct lbm_mix {
     d.Pr = d.RL[M] * d.thr;
     d.Cvr = cv;
     d.cE = d.RL[M + 1] - d.RL[M] * cv * T;
+    if (d.tvar) {
+      // temperature-dependent heats: U_a(T_r), the reference mixture's U(T_r)
+      double ur = 0.0;
+      for (int a = 0; a < lbm::MAXM; ++a) {
+        d.Uar[a] = a < M ? lbm::U_a64(d, a, T) : 0.0;
+        if (a < M) ur += d.Yr[a] * d.Uar[a];
+      }
+      d.Ur = ur;
+      d.cE = d.RL[M + 1] - d.RL[M] * ur;
+    }
     double pix = 0.0;
     for (int i = 0; i < 27; ++i) pix += base[M * 27 + i] * (double)(lbm::cx_of(i) * lbm::cx_of(i));
     d.cPi = pix - d.RL[M] * d.thr;
@@ -377,9 +395,9 @@ struct lbm_mix {
       if (rho - others > 0.0) r[p64.slaved] = rho - others;
     }
     for (int a = 0; a < M; ++a) tot += r[a];
-    double Y[lbm::MAXM], Cv = 0.0;
-    for (int a = 0; a < M; ++a) { Y[a] = r[a] / tot; Cv += Y[a] * p64.Cv_a[a]; }
-    return set_reference(Y, rhoE / (rho * Cv), rho);
+    double Y[lbm::MAXM];
+    for (int a = 0; a < M; ++a) Y[a] = r[a] / tot;
+    return set_reference(Y, lbm::T_from_energy64(p64, Y, M, rhoE / rho), rho);
   }
   // No deferred non-local terms are pending for a state set from outside.
   lbm_status clear_pending() {
@@ -616,6 +634,21 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     for (int a = 0; a < M; ++a) if (!(p->lambda[a] > 0.0)) return bad("lambda_a must be > 0");
   } else if (!(p->omega1_fixed < 2.0)) return bad("omega1_fixed must be in (0, 2)");
 
+  const bool tvar = p->cv_poly != nullptr;
+  if (tvar) {
+    if (p->cv_terms < 1 || p->cv_terms > 3) return bad("cv_terms must be 1..3 with cv_poly");
+    if (!(p->precision == LBM_PREC_FP64 || p->precision == LBM_PREC_FP32)) {
+      g_create_error = "temperature-dependent heats run with FP64 or FP32 storage";
+      return LBM_ERR_UNSUPPORTED;
+    }
+    if (walls || p->closure == LBM_CLOSURE_MLP) {
+      g_create_error = "temperature-dependent heats run on periodic grids with the exact closure";
+      return LBM_ERR_UNSUPPORTED;
+    }
+    for (int a = 0; a < M; ++a)
+      if (!(p->cv_poly[a * p->cv_terms] > 0.0)) return bad("cv_poly: the heat at T = 0 must be > 0");
+  }
+
   const lbm::KernelSet* ks = select_kernels(M, p->precision);
   if (!ks) { g_create_error = "no kernels built for this (M, precision)"; return LBM_ERR_UNSUPPORTED; }
   if (p->closure == LBM_CLOSURE_MLP && !ks->mlp_step_ok) {
@@ -665,6 +698,20 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
       }
       d.Cab64[a][b] = d.Cab[a][b];
     }
+  d.tvar = tvar ? 1 : 0;
+  d.nterm = tvar ? p->cv_terms : 1;
+  for (int a = 0; a < lbm::MAXM; ++a) {
+    for (int k = 0; k < 3; ++k) {
+      // per mass: C_{a,v}(T) = (R_U / m_a) sum_k c_ak T^k; U_a = T sum_k c_ak T^k R_U / (m_a (k + 1))
+      const double c = (a < M) ? (tvar ? (k < p->cv_terms ? p->cv_poly[a * p->cv_terms + k] : 0.0)
+                                       : (k == 0 ? p->cv_molar[a] : 0.0)) : 0.0;
+      d.cvp[a][k] = c * p->R_U / d.mass[a];
+      d.Uc[a][k] = d.cvp[a][k] / (k + 1);
+      d.Hc[a][k] = d.Uc[a][k] + (k == 0 && a < M ? d.R_a[a] : 0.0);
+    }
+    d.Uar[a] = 0.0;
+  }
+  d.Ur = 0.0;
   d.rho_eps = 1e-14;
   const bool store16 = p->precision == LBM_PREC_FP16_STORE || p->precision == LBM_PREC_BF16_STORE;
   d.rec_w = store16 ? lbm::eq_rec_width(M, d.weak) : 0;
@@ -1116,6 +1163,7 @@ lbm_status lbm_mix_batch_create(const lbm_mix_params* params, int ndomains, void
       return bad(LBM_ERR_ARG, "all domains must share M, precision and coupling");
   for (int d = 0; d < ndomains; ++d) {
     if (params[d].closure != LBM_CLOSURE_EXACT) return bad(LBM_ERR_UNSUPPORTED, "batched domains use the exact closure");
+    if (params[d].cv_poly) return bad(LBM_ERR_UNSUPPORTED, "batched domains use constant heats");
     for (int s = 0; s < 6; ++s)
       if (params[d].bc[s] != LBM_BC_PERIODIC) return bad(LBM_ERR_UNSUPPORTED, "batched domains are periodic");
   }

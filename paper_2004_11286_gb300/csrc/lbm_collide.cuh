@@ -308,7 +308,18 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 #pragma unroll
     for (int c = 0; c < 3; ++c) side[(SP_PHI + c) * N + n] = j[c] * a3 - rho * th.u[c] * th.u[c] * th.u[c];
     side[SP_COM * N + n] = Real(1) / om - Real(0.5);
-    side[SP_CP * N + n] = th.Cp;
+    if (!p.tvar) {
+      side[SP_CP * N + n] = th.Cp;
+    } else {
+      // sum_a H_a grad Y_a = sum_k T^k grad Phi_k with H = T (Phi_1 + Phi_2 T + Phi_3 T^2)
+      Real h1 = Real(0), h2 = Real(0), h3 = Real(0);
+#pragma unroll
+      for (int a = 0; a < M; ++a) { h1 += th.Y[a] * p.Hc[a][0]; h2 += th.Y[a] * p.Hc[a][1]; h3 += th.Y[a] * p.Hc[a][2]; }
+      side[SP_CP * N + n] = h1;
+      side[SP_HC2 * N + n] = h2;
+      side[SP_HC3 * N + n] = h3;
+      side[SP_T * N + n] = T;
+    }
     side[SP_S * N + n] = Real(0.5) * (Real(2) - om1) * P * T / th.theta;
     side[SP_TH * N + n] = th.theta;
   }
@@ -432,7 +443,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   // 1/(omega - omega_1)); the last, non-local term is deferred.
   {
     const Real theta = th.theta, thr = p.thr, dth = th.dtheta;
-    const Real hk = th.Cp * T + Real(0.5) * th.usq;
+    const Real hk = enthalpy<M, Real>(p, th) + Real(0.5) * th.usq;     // h = H + u^2/2
     const Real inv_theta = Real(1) / theta;
     const Real Gc = rho * (hk + theta) * Real(0.5) * inv_theta;
     const Real* u = th.u;
@@ -462,11 +473,20 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       qb[2] = q[2] - (u[0] * dP6[4] + u[1] * dP6[5] + u[2] * dP6[2]);
       Real hyv[3] = {Real(0), Real(0), Real(0)};
       const Real rY = p.weak ? rho / th.rho_sp : Real(1);   // rho Y_a = rY * rho_a
+      if (!p.tvar) {
 #pragma unroll
-      for (int a = 0; a < M; ++a) {
-        const Real sv = p.Cp_a[a] * th.rho_a[a];
+        for (int a = 0; a < M; ++a) {
+          const Real sv = p.Cp_a[a] * th.rho_a[a];          // H_a / T
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hyv[c] += sv * V[a][c];
+          for (int c = 0; c < 3; ++c) hyv[c] += sv * V[a][c];
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          const Real sv = enthalpy_a(p, a, T) * th.rho_a[a] / T;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) hyv[c] += sv * V[a][c];
+        }
       }
       const Real c1 = om1 * T * rY, dw = om - om1;
 #pragma unroll

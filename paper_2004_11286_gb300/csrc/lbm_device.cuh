@@ -20,8 +20,12 @@ constexpr int MAXM = 8;
 //   written by collide:  Phi_x,Phi_y,Phi_z (0-2), c_omega (3), C_p (4), s = c2/theta (5), theta (6)
 //   written by grad_GK:  G_x,G_y,G_z (7-9), K_x,K_y,K_z (10-12), theta of the sender (13)
 //   written by grad_X:   X_x,X_y,X_z (14-16)
-constexpr int NSIDE = 17;
-enum SidePlane { SP_PHI = 0, SP_COM = 3, SP_CP = 4, SP_S = 5, SP_TH = 6, SP_G = 7, SP_K = 10, SP_THR = 13, SP_X = 14 };
+//   with temperature-dependent heats, written by collide: the mixture
+//   enthalpy coefficients Phi_2, Phi_3 of H = T (Phi_1 + Phi_2 T + Phi_3 T^2)
+//   (Phi_1 in the C_p plane) and T (17-19)
+constexpr int NSIDE = 20;
+enum SidePlane { SP_PHI = 0, SP_COM = 3, SP_CP = 4, SP_S = 5, SP_TH = 6, SP_G = 7, SP_K = 10, SP_THR = 13, SP_X = 14,
+                 SP_HC2 = 17, SP_HC3 = 18, SP_T = 19 };
 
 // Velocity i = (cx+1) + 3(cy+1) + 9(cz+1), Eq. (d3q27vel).
 __host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
@@ -86,6 +90,13 @@ struct DevParams {
   // per-node equilibrium record (0 in the FP64 and FP32 modes).
   Real bref[MAXM + 2][4];
   int rec_w;
+  // Temperature-dependent heats (Sec. 3.1), tvar = 1: per mass and per species
+  // C_{a,v}(T) = sum_k cvp[a][k] T^k (k < nterm), U_a(T) = T sum_k Uc[a][k] T^k
+  // with Uc = cvp / (k + 1), H_a(T) = T sum_k Hc[a][k] T^k (Hc = Uc, plus R_a
+  // at k = 0); Uar[a] = U_a(T_r), Ur the reference mixture's U(T_r).
+  int tvar, nterm;
+  Real cvp[MAXM][3], Uc[MAXM][3], Hc[MAXM][3], Uar[MAXM];
+  Real Ur;
 };
 
 // ---------------------------------------------------------------------------
@@ -264,10 +275,41 @@ __device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Rea
   const Real dR = p.R_U * d_inv_m;
   th.Cv = Cv; th.Cp = Cp;
   th.usq = th.u[0] * th.u[0] + th.u[1] * th.u[1] + th.u[2] * th.u[2];
-  // Eq. (temperature2) with T0 = 0, rho E = rho (C_v T + u^2/2), written for
-  // T - Tr:  rho C_v (T - Tr) = rho E - rho u^2/2 - rho C_v Tr.
-  th.dT = (p.cE + rhoE_dev - Real(0.5) * rho * th.usq - rho_dev * p.Cvr * p.Tr - rho * dCv * p.Tr)
-        / (rho * Cv);
+  if (!p.tvar) {
+    // Eq. (temperature2) with T0 = 0, rho E = rho (C_v T + u^2/2), written for
+    // T - Tr:  rho C_v (T - Tr) = rho E - rho u^2/2 - rho C_v Tr.
+    th.dT = (p.cE + rhoE_dev - Real(0.5) * rho * th.usq - rho_dev * p.Cvr * p.Tr - rho * dCv * p.Tr)
+          / (rho * Cv);
+  } else {
+    // Eq. (temperature) with T0 = 0: rho U(T) = rho E - rho u^2/2, U = sum_a Y_a U_a,
+    // written for dT = T - Tr as  rho [U(T) - U(Tr)] = rhs  with
+    //   rhs = rho E - rho U(Tr) - rho u^2/2
+    //       = cE + (rho E - RL_g) - (rho - RL_f) U_r - rho sum_a (Y_a - Yr_a) U_a(Tr) - rho u^2/2
+    // and U(T) - U(Tr) = dT sum_k u_k (T^k + T^(k-1) Tr + ... + Tr^k) (no
+    // cancellation), solved by Newton's method (U' = C_v > 0).
+    Real um[3] = {Real(0), Real(0), Real(0)}, cm[3] = {Real(0), Real(0), Real(0)}, sdU = Real(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const Real dY = (th.rho_a_dev[a] - p.Yr[a] * sp_dev) * inv_sp;
+      sdU += dY * p.Uar[a];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { um[k] += th.Y[a] * p.Uc[a][k]; cm[k] += th.Y[a] * p.cvp[a][k]; }
+    }
+    const Real rhs = p.cE + rhoE_dev - rho_dev * p.Ur - rho * sdU - Real(0.5) * rho * th.usq;
+    const Real Tr = p.Tr;
+    Real dT = rhs / (rho * (cm[0] + Tr * (cm[1] + Tr * cm[2])));
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const Real T = Tr + dT;
+      const Real G = um[0] + um[1] * (T + Tr) + um[2] * (T * T + T * Tr + Tr * Tr);
+      const Real cvT = cm[0] + T * (cm[1] + T * cm[2]);
+      dT -= (rho * dT * G - rhs) / (rho * cvT);
+    }
+    th.dT = dT;
+    const Real T = Tr + dT;
+    th.Cv = cm[0] + T * (cm[1] + T * cm[2]);
+    th.Cp = th.Cv + th.R;
+  }
   th.T = p.Tr + th.dT;
   th.theta = th.R * th.T;
   th.dtheta = dR * th.T + p.Rr * th.dT;
@@ -290,6 +332,50 @@ __device__ __forceinline__ void thermo_state(const DevParams<Real>& p, const Rea
     }
     th.omega = Real(2) * th.P / (th.P + Real(2) * mu);            // Eq. (omega)
   }
+}
+
+// FP64 forms for initialisation, records and the host: per-mass heat, internal
+// energy and enthalpy of species a at T (Eqs. specUa, specHa, T0 = 0), and the
+// T that solves sum_a Y_a U_a(T) = e (Eq. temperature) by Newton's method.
+__host__ __device__ inline double cv_a64(const DevParams<double>& p, int a, double T) {
+  return p.tvar ? p.cvp[a][0] + T * (p.cvp[a][1] + T * p.cvp[a][2]) : p.Cv_a[a];
+}
+__host__ __device__ inline double U_a64(const DevParams<double>& p, int a, double T) {
+  return p.tvar ? T * (p.Uc[a][0] + T * (p.Uc[a][1] + T * p.Uc[a][2])) : p.Cv_a[a] * T;
+}
+__host__ __device__ inline double H_a64(const DevParams<double>& p, int a, double T) {
+  return U_a64(p, a, T) + p.R_a[a] * T;
+}
+__host__ __device__ inline double T_from_energy64(const DevParams<double>& p, const double* Y, int M, double e) {
+  double cv0 = 0.0;
+  for (int a = 0; a < M; ++a) cv0 += Y[a] * cv_a64(p, a, 0.0);
+  double T = e / cv0;
+  if (!p.tvar) return T;
+  for (int it = 0; it < 60; ++it) {
+    double U = 0.0, cv = 0.0;
+    for (int a = 0; a < M; ++a) { U += Y[a] * U_a64(p, a, T); cv += Y[a] * cv_a64(p, a, T); }
+    const double dT = (U - e) / cv;
+    T -= dT;
+    if (fabs(dT) <= 1e-15 * fabs(T)) break;
+  }
+  return T;
+}
+
+// Species enthalpy H_a(T) (Eq. specHa, T0 = 0): C_{a,p} T with constant
+// heats, T (Hc_0 + Hc_1 T + Hc_2 T^2) with temperature-dependent ones.
+template <class Real>
+__device__ __forceinline__ Real enthalpy_a(const DevParams<Real>& p, int a, Real T) {
+  if (!p.tvar) return p.Cp_a[a] * T;
+  return T * (p.Hc[a][0] + T * (p.Hc[a][1] + T * p.Hc[a][2]));
+}
+// Mixture enthalpy H = sum_a Y_a H_a (Eq. specH).
+template <int M, class Real>
+__device__ __forceinline__ Real enthalpy(const DevParams<Real>& p, const Thermo<M, Real>& th) {
+  if (!p.tvar) return th.Cp * th.T;
+  Real h = Real(0);
+#pragma unroll
+  for (int a = 0; a < M; ++a) h += th.Y[a] * enthalpy_a(p, a, th.T);
+  return h;
 }
 
 template <int M, class Real>

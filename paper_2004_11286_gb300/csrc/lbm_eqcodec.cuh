@@ -194,19 +194,20 @@ __device__ __forceinline__ EqRec<M> eq_record64(const DevParams<double>& p, cons
   double rsp = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) rsp += rho_a[a];
-  double inv_m = 0.0, Cv = 0.0, Cp = 0.0;
+  double inv_m = 0.0, Y[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    const double Y = rho_a[a] / rsp;
-    inv_m += Y * p.inv_mass[a];
-    Cv += Y * p.Cv_a[a];
-    Cp += Y * p.Cp_a[a];
+    Y[a] = rho_a[a] / rsp;
+    inv_m += Y[a] * p.inv_mass[a];
   }
   const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
   const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const double T = (rhoE / rho - 0.5 * usq) / Cv;          // Eq. (temperature2), T0 = 0
+  const double T = T_from_energy64(p, Y, M, rhoE / rho - 0.5 * usq);   // Eqs. (temperature), (temperature2)
   const double th = p.R_U * inv_m * T;
-  const double hk = Cp * T + 0.5 * usq;
+  double H = 0.0;
+#pragma unroll
+  for (int a = 0; a < M; ++a) H += Y[a] * H_a64(p, a, T);
+  const double hk = H + 0.5 * usq;
   const double Gc = rho * (hk + th) / (2.0 * th);
   EqRec<M> r;
 #pragma unroll

@@ -39,15 +39,15 @@ init_rec_kernel(const DevParams<double> p, float* __restrict__ side, const doubl
 #pragma unroll
   for (int c = 0; c < 3; ++c) u[c] = uin[c * N + n];
   const double T = Tin[n], rho = Pin[n] * m / (p.R_U * T);
-  double ra[M], Cv = 0.0;
+  double ra[M], Umix = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     const double Y = X[a] * p.mass[a] / m;
     ra[a] = Y * rho;
-    Cv += Y * p.Cv_a[a];
+    Umix += Y * U_a64(p, a, T);
   }
   const double j[3] = {rho * u[0], rho * u[1], rho * u[2]};
-  const double rhoE = rho * (Cv * T + 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  const double rhoE = rho * (Umix + 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
   store_rec<M>(eq_rec_buf(side, N, p.rec_w, 1), n, p.rec_w, p.weak, eq_record64<M>(p, ra, rho, j, rhoE, u));
 }
 
@@ -95,7 +95,13 @@ init_kernel(const DevParams<double> p, const DevParams<float> p32, Store* __rest
     Cp += Y[a] * p.Cp_a[a];
   }
   const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const double rhoE = rho * (Cv * T + 0.5 * usq);
+  double Umix = Cv * T, Hmix = Cp * T;                    // constant heats
+  if (p.tvar) {                                           // Eqs. specUa, specHa, Umix, specH
+    Umix = 0.0; Hmix = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) { Umix += Y[a] * U_a64(p, a, T); Hmix += Y[a] * H_a64(p, a, T); }
+  }
+  const double rhoE = rho * (Umix + 0.5 * usq);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     const double ra = Y[a] * rho, ze = p.R_a[a] * T;
@@ -116,7 +122,7 @@ init_kernel(const DevParams<double> p, const DevParams<float> p32, Store* __rest
     }
   }
   {
-    const double theta = R * T, hk = Cp * T + 0.5 * usq;
+    const double theta = R * T, hk = Hmix + 0.5 * usq;
     double Mt[6];
     Mt[0] = hk * (P + rho * u[0] * u[0]) + P * u[0] * u[0];
     Mt[1] = hk * (P + rho * u[1] * u[1]) + P * u[1] * u[1];
@@ -285,7 +291,7 @@ struct Launch {
     }
     if (c.ev) cudaEventRecord(c.ev[1], c.stream);
     // Row-blocked stencils (ROWV nodes per thread) where rows split evenly.
-    const bool rows = P(c).nx % ROWV == 0;
+    const bool rows = P(c).nx % ROWV == 0 && !P(c).tvar;
     if (rows) grad_GK_row_kernel<Real><<<grid_for(c.N / ROWV, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     else grad_GK_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     if (c.ev) cudaEventRecord(c.ev[2], c.stream);

@@ -185,19 +185,24 @@ __device__ __forceinline__ void load_state_moments(const DevParams<Real>& p, con
 // Stencil pass 1 (after a collision): G_alpha = c_omega d_alpha Phi_alpha (the
 // inner derivative of Eq. Xalpha) and K_alpha = s d_alpha C_p with s = c2 / theta;
 // the sender's theta is copied for the receivers' weights.
+// With temperature-dependent heats (tvar) the enthalpy field differentiated
+// is H-like: Phi_1 + T_n Phi_2 + T_n^2 Phi_3 of the neighbours with this
+// node's T_n, so that K = s sum_k T^(k-1) grad Phi_k = (s / T) sum_a H_a grad Y_a.
 template <class Real, class G>
-__device__ __forceinline__ void grad_GK_node(const G& p, Real* __restrict__ side, long long n) {
+__device__ __forceinline__ void grad_GK_node(const G& p, Real* __restrict__ side, long long n, bool tvar = false) {
   if (n >= p.N) return;
   const long long N = p.N;
   const Nbr nb = make_nbr(p, n);
   Real d[3] = {Real(0), Real(0), Real(0)}, dc[3] = {Real(0), Real(0), Real(0)};
+  const Real Tn = tvar ? side[SP_T * N + n] : Real(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     if (i == 13) continue;
     const long long nn = nb.idx(cx, cy, cz);
     const Real w = iso_w<Real>(i);
-    const Real cp = side[SP_CP * N + nn];
+    Real cp = side[SP_CP * N + nn];
+    if (tvar) cp += Tn * (side[SP_HC2 * N + nn] + Tn * side[SP_HC3 * N + nn]);
     // beyond a wall the mirror image of Phi_x is odd, the other fields even
     const bool mirror = (cx < 0 && (nb.wall & 1u)) || (cx > 0 && (nb.wall & 2u));
     if (cx) {
@@ -444,7 +449,7 @@ grad_X_row_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ 
 template <class Real>
 __global__ void __launch_bounds__(BLOCK_LIGHT)
 grad_GK_kernel(const __grid_constant__ DevParams<Real> p, Real* __restrict__ side) {
-  grad_GK_node<Real>(p, side, gtid());
+  grad_GK_node<Real>(p, side, gtid(), p.tvar != 0);
 }
 template <class Real>
 __global__ void __launch_bounds__(BLOCK_LIGHT)

@@ -270,6 +270,22 @@ def khi_n2_h2o(shape=(200, 800, 800), reynolds: float = 11963.46, mach_r: float 
     return Workload("khi_n2_h2o", mm, cv, D, mu, lam, X, u, T, P, steps)
 
 
+def variable_heats(molar_mass, seed: int = 0, T_ref: float = T_AMBIENT) -> np.ndarray:
+    """Synthetic temperature-dependent molar heats for Sec. 3.1 (no
+    thermochemical data exist here): C-bar_{a,v}(T) / R_U = c0 + c1 T + c2 T^2
+    per species, with the value at T_ref the molecular-identity constant of
+    cv_for_mass and slopes drawn from `seed` so the heat changes by -10 % ..
+    +40 % between T = 0 and 2 T_ref while staying positive.  Returns (M, 3)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in np.asarray(molar_mass, dtype=np.float64):
+        c_ref = cv_for_mass(float(m))
+        s1, s2 = rng.uniform(-0.05, 0.2), rng.uniform(0.0, 0.1)       # fractional changes per T_ref, per T_ref^2
+        c1, c2 = s1 * c_ref / T_ref, s2 * c_ref / T_ref ** 2
+        out.append([c_ref - c1 * T_ref - c2 * T_ref ** 2, c1, c2])
+    return np.array(out)
+
+
 def random_mixture(M: int = 8, n: int = 192, seed: int = 7, steps: int = 3000,
                    shape: Optional[tuple] = None, modes: int = 16, velocity: float = 0.0,
                    field_seed: Optional[int] = None, amplitude: float = 0.5) -> Workload:
