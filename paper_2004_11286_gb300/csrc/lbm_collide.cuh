@@ -78,6 +78,11 @@ constexpr int collide_min_blocks() {
 #ifndef LBM_SPECIES_LOOP_MIN_M
 #define LBM_SPECIES_LOOP_MIN_M 4
 #endif
+// Unrolled species update with per-axis factor tables (1) or the factors
+// recomputed at every velocity (0).
+#ifndef LBM_SPECIES_AXIS_TABLES
+#define LBM_SPECIES_AXIS_TABLES 1
+#endif
 
 template <int M, class Real, int CL = 0, class Store = Real>
 constexpr size_t collide_stage_bytes() {
@@ -624,6 +629,56 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         }
         species_velocity(i, cx, cy, cz, node, slot);
       }
+    } else if constexpr (LBM_SPECIES_AXIS_TABLES) {
+      // Unrolled velocities, every product-form factor taken from per-axis
+      // tables: each 1-D factor has one value per axis and c in {-1, 0, +1},
+      // formed once per species instead of once per velocity.
+      //   A = Psi_c(u, z)   T = Psi_c(u) - Psi_c(u + V)   D = A - Psi_c(0, zr)   R = Psi_c(0, zr)
+      Real A[M][3][3], Tt[M][3][3], Da[M][3][3], Rr[M][2];
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        const Real z = zr[b] + dz[b];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+          for (int c = -1; c <= 1; ++c) {
+            A[b][ax][c + 1] = pf_a<Real>(c, th.u_sp[ax], x2[ax], z);
+            Tt[b][ax][c + 1] = pf_v<Real>(c, V[b][ax], ev[b][ax]);
+            Da[b][ax][c + 1] = pf_da<Real>(c, th.u_sp[ax], x2[ax], dz[b]);
+          }
+        Rr[b][0] = pf_r<Real>(0, zr[b]);
+        Rr[b][1] = pf_r<Real>(1, zr[b]);
+      }
+      static_for<0, Q>([&](auto I_) {
+        constexpr int i = decltype(I_)::value;
+        if constexpr (i != 13) {
+          constexpr int cx = cx_of(i) + 1, cy = cy_of(i) + 1, cz = cz_of(i) + 1;
+          long long node; int slot;
+          aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
+          Real Dif[M];
+#pragma unroll
+          for (int b = 0; b < M; ++b) {
+            const Real ayz = A[b][1][cy] * A[b][2][cz];
+            const Real sx = A[b][0][cx] - Tt[b][0][cx], sy = A[b][1][cy] - Tt[b][1][cy];
+            Dif[b] = th.rho_a[b] * (Tt[b][0][cx] * ayz + sx * (Tt[b][1][cy] * A[b][2][cz] + sy * Tt[b][2][cz]));
+          }
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            Real F = Real(0);
+#pragma unroll
+            for (int b = 0; b < M; ++b) F += p.Cab[a][b] * Dif[b];
+            F *= tY[a];
+            const Real rx = Rr[a][cx == 1 ? 0 : 1], ry = Rr[a][cy == 1 ? 0 : 1], rz = Rr[a][cz == 1 ? 0 : 1];
+            const Real d = Da[a][0][cx] * A[a][1][cy] * A[a][2][cz]
+                         + rx * (Da[a][1][cy] * A[a][2][cz] + ry * Da[a][2][cz]);
+            const Real e = th.rho_a[a] * d + th.rho_a_dev[a] * (rx * ry * rz);
+            s_e[a] += e; s_F[a] += F;
+            const Real kv = species_val(a, i, cx - 1);
+            const Real out = kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F;
+            if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
+          }
+        }
+      });
     } else {
       static_for<0, Q>([&](auto I_) {
         constexpr int i = decltype(I_)::value;
