@@ -61,6 +61,7 @@ void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   }
   for (int L = 0; L < lbm::MAXM + 2; ++L) {
     d.RL[L] = (Real)s.RL[L]; d.scale[L] = (Real)s.scale[L]; d.inv_scale[L] = (Real)s.inv_scale[L];
+    d.RL64[L] = s.RL[L];
   }
   for (int L = 0; L < lbm::MAXM + 2; ++L)
     for (int k = 0; k < 4; ++k) d.bref[L][k] = (Real)s.bref[L][k];

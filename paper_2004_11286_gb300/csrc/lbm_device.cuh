@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace lbm {
 
@@ -77,6 +78,7 @@ struct DevParams {
   // Reference rest state.  Populations are stored as deviations d = f - b
   // from each lattice's rest equilibrium b at this state; RL[L] = sum_i b_Li.
   Real RL[MAXM + 2];
+  double RL64[MAXM + 2]; // the same in FP64 (the FP64 re-solve of the SM system)
   Real Yr[MAXM];         // reference mass fractions, RL[a] / sum_a RL[a]
   Real Tr, Rr, thr, Pr;  // reference T, mixture R, theta = R T, P = RL[f] theta
   Real Cvr;              // reference mixture C_v
@@ -428,10 +430,34 @@ __device__ __forceinline__ void sm_eliminate(T (&A)[M][M], T (&r)[M][3], T (&J)[
   }
 }
 
-template <int M, class Real>
+// FP64 species moments for the FP64 re-solve: densities, momenta, the
+// velocity the species see and their total density (Eqs. rhoMATCH, uMATCH
+// under strong coupling; Eqs. rhoSPEC, uSPEC under weak coupling).
+template <int M>
+struct SpMoments64 {
+  double rho_a[M], ja[M][3], u[3], rho_sp;
+};
+// Default source of the FP64 re-solve's inputs: the arithmetic-type moments.
+struct FromThermo {};
+
+// The exact solve.  In the FP32 paths a system whose condition bound
+// exceeds p.cond_bound is solved in FP64 instead.  Its solution splits into
+// the components the system damps (by 1/tau) and the one it passes
+// unchanged: A Y = Y, so r + s Y gives J + s Y, and the component of r along
+// sum_a r_a = j - rho u (under either coupling) is zero in exact arithmetic.
+// Formed in FP32 that component is rounding noise of the size of eps |j|, a
+// common shift of every species velocity that swamps diffusion velocities of
+// order r tau.  So the FP64 system takes
+//   * `mom` (an SpMoments64 filler): moments summed in FP64 from the stored
+//     populations, where sum_a r_a vanishes to FP64 rounding (the readers);
+//   * FromThermo: the FP32 moments with that component removed,
+//     r_a -= Y_a sum_b r_b (the collide: there the shift is harmless, the force
+//     of Eq. fstar1 multiplies it by 1/tau_ab and the update by beta_a - 1,
+//     about -2 tau_a, and re-reading the stage in FP64 costs 2 % of the step).
+template <int M, class Real, class Mom = FromThermo>
 __device__ __forceinline__ void sm_solve(const DevParams<Real>& p, const Thermo<M, Real>& th,
                                          const Real (&itab)[M][M], const Real (&ja)[M][3],
-                                         Real (&J)[M][3]) {
+                                         Real (&J)[M][3], const Mom& mom = Mom{}) {
   Real A[M][M], r[M][3];
   Real cond = Real(0);
 #pragma unroll
@@ -451,30 +477,57 @@ __device__ __forceinline__ void sm_solve(const DevParams<Real>& p, const Thermo<
   }
   if constexpr (sizeof(Real) == 4) {
     if (cond + Real(1) > p.cond_bound) {
-    // Ill-conditioned system in the FP32 paths: re-solve in FP64.
-    double A64[M][M], r64[M][3], J64[M][3];
-    double T = (double)th.T, m = (double)th.m;
+      // Ill-conditioned system in the FP32 paths: re-solve in FP64.
+      double A64[M][M], r64[M][3], J64[M][3], Y64[M];
+      double tm;
+      if constexpr (std::is_same<Mom, FromThermo>::value) {
+        tm = (double)p.R_U * (double)th.T * (double)th.m;
 #pragma unroll
-    for (int a = 0; a < M; ++a) {
-      double diag = 1.0;
+        for (int a = 0; a < M; ++a) {
+          Y64[a] = (double)th.Y[a];
 #pragma unroll
-      for (int b = 0; b < M; ++b) {
-        if (b != a) {
-          double it = (double)p.R_U * T * m * p.Cab64[a][b];
-          diag += 0.5 * it * (double)th.Y[b];
-          A64[a][b] = -0.5 * it * (double)th.Y[a];
+          for (int c = 0; c < 3; ++c) r64[a][c] = (double)ja[a][c] - (double)th.rho_a[a] * (double)th.u_sp[c];
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double sr = 0.0;
+#pragma unroll
+          for (int a = 0; a < M; ++a) sr += r64[a][c];
+#pragma unroll
+          for (int a = 0; a < M; ++a) r64[a][c] -= Y64[a] * sr;
+        }
+      } else {
+        SpMoments64<M> m;
+        mom(m);
+        double inv_m = 0.0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          Y64[a] = m.rho_a[a] / m.rho_sp;
+          inv_m += Y64[a] / (double)p.mass[a];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) r64[a][c] = m.ja[a][c] - m.rho_a[a] * m.u[c];
+        }
+        tm = (double)p.R_U * (double)th.T / inv_m;
       }
-      A64[a][a] = diag;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r64[a][c] = (double)ja[a][c] - (double)th.rho_a[a] * (double)th.u_sp[c];
-    }
-    sm_eliminate<M, double>(A64, r64, J64);
+      for (int a = 0; a < M; ++a) {
+        double diag = 1.0;
 #pragma unroll
-    for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          if (b != a) {
+            const double it = tm * p.Cab64[a][b];
+            diag += 0.5 * it * Y64[b];
+            A64[a][b] = -0.5 * it * Y64[a];
+          }
+        }
+        A64[a][a] = diag;
+      }
+      sm_eliminate<M, double>(A64, r64, J64);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) J[a][c] = (Real)J64[a][c];
-    return;
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) J[a][c] = (Real)J64[a][c];
+      return;
     }
   }
   sm_eliminate<M, Real>(A, r, J);

@@ -9,6 +9,67 @@
 
 namespace lbm {
 
+// FP64 species and momentum-lattice moments of node n read again from the
+// stored populations (with their pending terms and shifts), for the FP64
+// re-solve of an ill-conditioned system in the FP32 paths (Eqs. rhoMATCH,
+// uMATCH or rhoSPEC, uSPEC).  Out of line: only those nodes run it.
+template <int M, class Real, class Store>
+__device__ __noinline__ void state_moments64(const DevParams<Real>& p, const Store* __restrict__ pops,
+                                             const Real* __restrict__ side, int parity, long long n,
+                                             SpMoments64<M>* out) {
+  const long long N = p.N;
+  const Nbr nb = make_nbr(p, n);
+  SpMoments64<M> m;
+  double rf = 0.0, jf[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < M; ++a) { m.rho_a[a] = 0.0; m.ja[a][0] = m.ja[a][1] = m.ja[a][2] = 0.0; }
+  static_for<0, Q>([&](auto I_) {
+    constexpr int i = decltype(I_)::value;
+    constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+    long long node; int slot;
+    aa_read_loc<true>(parity, nb, n, i, node, slot);
+    Real cf, cg, sh[M + 2];
+    incoming_terms<M, Real, Store, i>(p, side, nb, n, parity, cf, cg, sh);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const double v = (double)codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a) + (double)sh[a];
+      m.rho_a[a] += v;
+      m.ja[a][0] += cx * v; m.ja[a][1] += cy * v; m.ja[a][2] += cz * v;
+    }
+    const double fv = (double)codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + (double)cf
+                    + (double)sh[M];
+    rf += fv;
+    jf[0] += cx * fv; jf[1] += cy * fv; jf[2] += cz * fv;
+  });
+#pragma unroll
+  for (int a = 0; a < M; ++a) m.rho_a[a] += p.RL64[a];
+  if (!p.weak) {
+    const double rho = p.RL64[M] + rf;
+    double ro = 0.0, o[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a != p.slaved) { ro += m.rho_a[a]; o[0] += m.ja[a][0]; o[1] += m.ja[a][1]; o[2] += m.ja[a][2]; }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+      if (a == p.slaved) {
+        m.rho_a[a] = rho - ro;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m.ja[a][c] = jf[c] - o[c];
+      }
+    m.rho_sp = rho;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.u[c] = jf[c] / rho;
+  } else {
+    double rs = 0.0, js[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < M; ++a) { rs += m.rho_a[a]; js[0] += m.ja[a][0]; js[1] += m.ja[a][1]; js[2] += m.ja[a][2]; }
+    m.rho_sp = rs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.u[c] = js[c] / rs;
+  }
+  *out = m;
+}
+
 // Observables: rho, u, T, P, X_a, Y_a, V_a (Sec. 2.1, Eq. temperature2, Eq. transform12).
 template <int M, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK)
@@ -41,7 +102,8 @@ moments_kernel(const DevParams<Real> p, const Store* __restrict__ pops, const Re
 #pragma unroll
     for (int b = 0; b < M; ++b) itab[a][b] = tm * p.Cab[a][b];
   Real J[M][3];
-  sm_solve<M, Real>(p, th, itab, ja, J);
+  auto moments64 = [&](SpMoments64<M>& m) { state_moments64<M, Real, Store>(p, pops, side, parity, n, &m); };
+  sm_solve<M, Real>(p, th, itab, ja, J, moments64);
   // rho, T and P leave as the reference value plus the state's deviation,
   // summed in FP64, so the output carries the deviation's own precision
   // rather than the rounding of the full value in the arithmetic type.

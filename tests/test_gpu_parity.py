@@ -384,6 +384,54 @@ def test_degenerate_grids_match_oracle(shape, precision):
 # FP32 paths: the M x M system re-solved in FP64 where its condition bound
 # exceeds fp64_cond_bound (1.0 sends every node there).
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("coupling", ["strong", "weak"])
+@pytest.mark.parametrize("shape", [(4, 5, 6), (2, 3, 128)])
+def test_fp64_fallback_on_ill_conditioned_system(shape, coupling):
+    """Ternary mixture with D_12 = 1e-6 and D_13 = 1e-5: 1/tau_12 is near 2e4
+    and the system of Eq. (transform12) has a condition bound near 1e4.
+
+    Its solution splits into the components the system damps (by 1/tau) and
+    the one it passes unchanged, along sum_a r_a = j - rho u, which is zero in
+    exact arithmetic.  Formed in FP32, that component is rounding noise of
+    the size of eps |j|: a common shift of every species velocity, which
+    swamps diffusion velocities V_a of order r / (1/tau) (an observable of
+    Sec. 2.5.3).  The FP64 re-solve forms r from the populations summed in
+    FP64, where the component vanishes to FP64 rounding, and must give V_a
+    to FP32 accuracy.  In the populations the shift is harmless: the force of
+    Eq. (fstar1) multiplies it by 1/tau_ab and the update by beta_a - 1, about
+    -2 tau_a, so both solves leave them at FP32 storage accuracy.
+    (2, 3, 128) takes the bulk row-load path, whose odd parity reads the
+    stage shifted."""
+    wl = W.random_mixture(M=3, shape=shape, seed=953, velocity=0.03)
+    D = wl.D.copy()
+    D[0, 1] = D[1, 0] = 1e-6
+    D[0, 2] = D[2, 0] = 1e-5
+    wl.D = D
+    prm = oracle_params(wl, coupling=coupling)
+    pops = _perturbed_state(wl, prm, seed=3)
+    refs = [O.step(pops, prm)]
+    refs.append(O.step(refs[0], prm))
+    Vref = [O.macroscopic(r, prm)["V"] for r in refs]
+    err_f, err_V = {}, {}
+    for name, bound in (("fp32 solve", 1e30), ("fp64 re-solve", 1.0), ("default bound", 0.0)):
+        h = gpu_handle(wl, "fp32", coupling=coupling, fp64_cond_bound=bound)
+        h.set_populations(pops)
+        ef, ev = [], []
+        for ref, vr in zip(refs, Vref):        # both streaming parities
+            h.step(1)
+            ef.append(rel(h.populations()[:3], ref[:3]))
+            ev.append(rel(h.moments_dict()["V"], vr))
+        err_f[name], err_V[name] = max(ef), max(ev)
+        h.close()
+    print(shape, coupling, "species populations", {k: f"{v:.2e}" for k, v in err_f.items()},
+          "V_a", {k: f"{v:.2e}" for k, v in err_V.items()})
+    for name in err_f:
+        assert err_f[name] < TOL["fp32"], name
+    assert err_V["fp64 re-solve"] < 1e-4
+    assert err_V["default bound"] < 1e-4
+    assert err_V["fp64 re-solve"] < 0.1 * err_V["fp32 solve"]
+
+
 @pytest.mark.parametrize("M", [3, 8])
 def test_fp64_solve_fallback_matches_oracle(M):
     wl = W.random_mixture(M=M, shape=(4, 5, 6), seed=950 + M, velocity=0.03)
