@@ -42,19 +42,30 @@ constexpr int collide_block() {
        : (per * 64 <= 113 * 1024 ? 64 : 32);
 }
 
+// Store addresses recomputed in each store phase from an opaque copy of the
+// node index (1), or left to the compiler, which at even parity (every
+// address the node's own) keeps load addresses live for the stores (0).
+#ifndef LBM_OPAQUE_STORE
+#define LBM_OPAQUE_STORE 2
+#endif
+template <int M, class Store>
+constexpr bool kOpaqueStore = LBM_OPAQUE_STORE == 2 ? (M >= 3 || sizeof(Store) == 2) : LBM_OPAQUE_STORE != 0;
+
 // Minimum resident blocks per SM asked of the register allocator, capped by
 // what the shared-memory tile allows (LBM_COLLIDE_MINB overrides).  Measured
-// on GB300: M <= 2, 3 (168 registers per thread for 128-thread blocks; the
-// 128^3 M = 2 FP32 pulse 3570 MLUPS against 3245 (1), 3246 (2), 2956 (4));
-// M >= 3, 2 (255 registers, no spills; 128^3 M = 3 mixture FP32 2552
-// against 2475 at 3).
+// on GB300 with 128-node blocks:
+//   M <= 2, FP32 storage: 3 (168 registers; 256^3 shear layer 4321 MLUPS
+//     against 3443 at 4, where the odd-parity kernel spills);
+//   M <= 2, 16-bit storage: 4 (128 registers; 2411 against 2158 at 3);
+//   M = 3: 3 (128^3 mixture FP32 2987 against 2961 at 2, BF16 1451 against 977);
+//   M >= 4: 2 (255 registers; the stage allows no more from M = 5 on).
 template <int M, class Real, int CL = 0, class Store = Real>
 constexpr int collide_min_blocks() {
   if constexpr (CL) return 1;
 #ifdef LBM_COLLIDE_MINB
   constexpr int want = LBM_COLLIDE_MINB;
 #else
-  constexpr int want = M <= 2 ? 3 : 2;
+  constexpr int want = M <= 2 ? (sizeof(Store) == 2 ? 4 : 3) : (M == 3 ? 3 : 2);
 #endif
   constexpr long long bytes = stage_per_node<M, Real, Store>() * collide_block<M, Real, 0, Store>();
   constexpr long long nb = (227LL * 1024) / bytes;
@@ -82,6 +93,11 @@ constexpr int collide_min_blocks() {
 // recomputed at every velocity (0).
 #ifndef LBM_SPECIES_AXIS_TABLES
 #define LBM_SPECIES_AXIS_TABLES 1
+#endif
+// FP32, M = 2 or 3: species 0 and 1 updated as one pair of lanes of the
+// paired FP32 instructions (1), or one species at a time (0).
+#ifndef LBM_SPECIES_PAIRS
+#define LBM_SPECIES_PAIRS 1
 #endif
 
 template <int M, class Real, int CL = 0, class Store = Real>
@@ -414,11 +430,12 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     Real s_f = Real(0);
     const Real x2[3] = {th.u[0] * th.u[0], th.u[1] * th.u[1], th.u[2] * th.u[2]};
     const Nbr nbw = opaque(nb);
+    const long long nw = kOpaqueStore<M, Store> ? opaque_idx(n) : n;
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
       if constexpr (i != 13) {
         long long node; int slot;
-        aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
+        aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
         const Real e = rho * pf_diff<Real, i>(th.u, x2, p.thr, th.dtheta) + rho_dev * pf_ref<Real, i>(p.thr);
         s_f += e;
         const Real fv = cell(M, i, cx_of(i));
@@ -427,7 +444,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       }
     });
     long long node; int slot;
-    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, nw, 13, node, slot);
     const Real fv = cell(M, 13, 0);
     const Real e13 = rho_dev - s_f;
     const Real out = fv + om * (e13 - fv);
@@ -515,12 +532,13 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     const Real d0 = -dth, d1 = Real(0.5) * dth;
     Real s_g = Real(0);
     const Nbr nbw = opaque(nb);
+    const long long nw = kOpaqueStore<M, Store> ? opaque_idx(n) : n;
     static_for<0, Q>([&](auto I_) {
       constexpr int i = decltype(I_)::value;
       if constexpr (i != 13) {
         constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
         long long node; int slot;
-        aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
+        aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
         const Real uc = dotc<Real, i>(th.u);
         const Real cc = Real(0.5) * Real(c2_of(i));
         const Real ucu = Gc * uc * uc * inv_theta;
@@ -541,7 +559,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       }
     });
     long long node; int slot;
-    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, nw, 13, node, slot);
     const Real gv = cell(M + 1, 13, 0);
     const Real e13 = rhoE_dev - s_g;
     const Real out = gv + om * (e13 - gv);
@@ -575,6 +593,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 #pragma unroll
     for (int a = 0; a < M; ++a) { s_e[a] = Real(0); s_F[a] = Real(0); }
     const Nbr nbw = opaque(nb);
+    const long long nw = kOpaqueStore<M, Store> ? opaque_idx(n) : n;
     // One velocity of the species update.  With many species the velocity
     // loop runs at run time: unrolled, the compiler keeps every species' axis
     // factors of all 26 velocities live at once and spills.
@@ -620,7 +639,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
         long long node; int slot;
         if (PAR == 0 || (WALL && leaves_to_wall(nbw, i))) {
-          node = n; slot = Q - 1 - i;
+          node = nw; slot = Q - 1 - i;
         } else {
           const unsigned xs = cx < 0 ? nbw.xs[0] : (cx > 0 ? nbw.xs[2] : nbw.xs[1]);
           const unsigned ys = cy < 0 ? nbw.ys[0] : (cy > 0 ? nbw.ys[2] : nbw.ys[1]);
@@ -629,6 +648,98 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         }
         species_velocity(i, cx, cy, cz, node, slot);
       }
+    } else if constexpr (LBM_SPECIES_PAIRS && std::is_same<Real, float>::value && M >= 2 && M <= 3) {
+      // Per-axis factor tables as below; species 0 and 1 run as the two lanes
+      // of paired FP32 instructions (for a pair, the lanes are species 0, 1 of
+      // the same velocity), species 2 (M = 3) alone.
+      //   A = Psi_c(u, z)   T = Psi_c(u) - Psi_c(u + V)   D = A - Psi_c(0, zr)   R = Psi_c(0, zr)
+      float2 A2[3][3], T2[3][3], D2[3][3], R2[2];
+      float A[3][3], Tt[3][3], Da[3][3], Rr[2];    // species 2 (M = 3)
+      {
+        const Real z0 = zr[0] + dz[0], z1 = zr[1] + dz[1];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+          for (int c = -1; c <= 1; ++c) {
+            A2[ax][c + 1] = make_float2(pf_a<Real>(c, th.u_sp[ax], x2[ax], z0), pf_a<Real>(c, th.u_sp[ax], x2[ax], z1));
+            T2[ax][c + 1] = make_float2(pf_v<Real>(c, V[0][ax], ev[0][ax]), pf_v<Real>(c, V[1][ax], ev[1][ax]));
+            D2[ax][c + 1] = make_float2(pf_da<Real>(c, th.u_sp[ax], x2[ax], dz[0]),
+                                        pf_da<Real>(c, th.u_sp[ax], x2[ax], dz[1]));
+          }
+        R2[0] = make_float2(pf_r<Real>(0, zr[0]), pf_r<Real>(0, zr[1]));
+        R2[1] = make_float2(pf_r<Real>(1, zr[0]), pf_r<Real>(1, zr[1]));
+        if constexpr (M == 3) {
+          const Real z2 = zr[2] + dz[2];
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int c = -1; c <= 1; ++c) {
+              A[ax][c + 1] = pf_a<Real>(c, th.u_sp[ax], x2[ax], z2);
+              Tt[ax][c + 1] = pf_v<Real>(c, V[2][ax], ev[2][ax]);
+              Da[ax][c + 1] = pf_da<Real>(c, th.u_sp[ax], x2[ax], dz[2]);
+            }
+          Rr[0] = pf_r<Real>(0, zr[2]);
+          Rr[1] = pf_r<Real>(1, zr[2]);
+        }
+      }
+      // F_a = sum_b K_ab Dif_b with K_ab = tY_a C_ab = Y_a / tau_ab
+      float K[M][M];
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) K[a][b] = tY[a] * p.Cab[a][b];
+      const float2 rho2 = make_float2(th.rho_a[0], th.rho_a[1]);
+      const float2 rd2 = make_float2(th.rho_a_dev[0], th.rho_a_dev[1]);
+      const float2 bb2 = make_float2(Real(2) * beta[0], Real(2) * beta[1]);
+      const float2 bm2 = make_float2(beta[0] - Real(1), beta[1] - Real(1));
+      float2 se2 = make_float2(0.f, 0.f), sF2 = make_float2(0.f, 0.f);
+      static_for<0, Q>([&](auto I_) {
+        constexpr int i = decltype(I_)::value;
+        if constexpr (i != 13) {
+          constexpr int cx = cx_of(i) + 1, cy = cy_of(i) + 1, cz = cz_of(i) + 1;
+          constexpr int kx = cx == 1 ? 0 : 1, ky = cy == 1 ? 0 : 1, kz = cz == 1 ? 0 : 1;
+          long long node; int slot;
+          aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
+          const float2 ayz = mul2(A2[1][cy], A2[2][cz]);
+          const float2 sx = sub2(A2[0][cx], T2[0][cx]), sy = sub2(A2[1][cy], T2[1][cy]);
+          const float2 in = fma2(sy, T2[2][cz], mul2(T2[1][cy], A2[2][cz]));
+          const float2 dif = mul2(rho2, fma2(T2[0][cx], ayz, mul2(sx, in)));
+          float dif_2 = 0.f, ayz_2 = 0.f;
+          if constexpr (M == 3) {
+            ayz_2 = A[1][cy] * A[2][cz];
+            const float tsx = A[0][cx] - Tt[0][cx], tsy = A[1][cy] - Tt[1][cy];
+            dif_2 = th.rho_a[2] * (Tt[0][cx] * ayz_2 + tsx * (Tt[1][cy] * A[2][cz] + tsy * Tt[2][cz]));
+          }
+          float F0 = K[0][0] * dif.x + K[0][1] * dif.y, F1 = K[1][0] * dif.x + K[1][1] * dif.y;
+          if constexpr (M == 3) { F0 += K[0][2] * dif_2; F1 += K[1][2] * dif_2; }
+          const float2 F = make_float2(F0, F1);
+          const float2 rx = R2[kx], ry = R2[ky], rz = R2[kz];
+          const float2 t1 = fma2(ry, D2[2][cz], mul2(D2[1][cy], A2[2][cz]));
+          const float2 d = fma2(D2[0][cx], ayz, mul2(rx, t1));
+          const float2 e = fma2(rho2, d, mul2(rd2, mul2(mul2(rx, ry), rz)));
+          se2 = add2(se2, e);
+          sF2 = add2(sF2, F);
+          const float2 kv = make_float2(species_val(0, i, cx - 1), species_val(1, i, cx - 1));
+          const float2 out = fma2(bm2, F, fma2(bb2, sub2(e, kv), kv));
+          const float2 st = EQ ? sub2(out, e) : out;
+          if (active) {
+            codec_store<Store, Real>(p, pops, (0 * Q + slot) * N + node, 0, st.x);
+            codec_store<Store, Real>(p, pops, (1 * Q + slot) * N + node, 1, st.y);
+          }
+          if constexpr (M == 3) {
+            const float F2 = K[2][0] * dif.x + K[2][1] * dif.y + K[2][2] * dif_2;
+            const float rx2 = Rr[kx], ry2 = Rr[ky], rz2 = Rr[kz];
+            const float d2 = Da[0][cx] * ayz_2 + rx2 * (Da[1][cy] * A[2][cz] + ry2 * Da[2][cz]);
+            const float e2 = th.rho_a[2] * d2 + th.rho_a_dev[2] * (rx2 * ry2 * rz2);
+            s_e[2] += e2; s_F[2] += F2;
+            const float kv2 = species_val(2, i, cx - 1);
+            const float out2 = kv2 + Real(2) * beta[2] * (e2 - kv2) + (beta[2] - Real(1)) * F2;
+            if (active) codec_store<Store, Real>(p, pops, (2 * Q + slot) * N + node, 2, EQ ? out2 - e2 : out2);
+          }
+        }
+      });
+      s_e[0] += se2.x; s_e[1] += se2.y;
+      s_F[0] += sF2.x; s_F[1] += sF2.y;
     } else if constexpr (LBM_SPECIES_AXIS_TABLES) {
       // Unrolled velocities, every product-form factor taken from per-axis
       // tables: each 1-D factor has one value per axis and c in {-1, 0, +1},
@@ -654,7 +765,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         if constexpr (i != 13) {
           constexpr int cx = cx_of(i) + 1, cy = cy_of(i) + 1, cz = cz_of(i) + 1;
           long long node; int slot;
-          aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
+          aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
           Real Dif[M];
 #pragma unroll
           for (int b = 0; b < M; ++b) {
@@ -684,13 +795,13 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         constexpr int i = decltype(I_)::value;
         if constexpr (i != 13) {
           long long node; int slot;
-          aa_write_loc<WALL>(PAR, nbw, n, i, node, slot);
+          aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
           species_velocity(i, cx_of(i), cy_of(i), cz_of(i), node, slot);
         }
       });
     }
     long long node; int slot;
-    aa_write_loc<WALL>(PAR, nbw, n, 13, node, slot);
+    aa_write_loc<WALL>(PAR, nbw, nw, 13, node, slot);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const Real e = th.rho_a_dev[a] - s_e[a];

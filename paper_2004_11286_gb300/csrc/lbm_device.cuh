@@ -155,6 +155,15 @@ __device__ __forceinline__ Nbr make_nbr(const P& p, long long n_) {
   return b;
 }
 
+// A copy of a node index that the compiler cannot identify with the
+// original (see opaque below): at even parity every store address of a
+// phase is the node's own, and would otherwise be kept live from the loads.
+__device__ __forceinline__ long long opaque_idx(long long a) {
+  long long b;
+  asm volatile("mov.b64 %0, %1;" : "=l"(b) : "l"(a));
+  return b;
+}
+
 // A copy of the neighbour table that the compiler cannot identify with the
 // original, so addresses recomputed from it are not merged with (and kept
 // live from) those of an earlier phase of the same kernel.

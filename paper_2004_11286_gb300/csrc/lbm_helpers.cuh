@@ -171,4 +171,19 @@ __device__ __forceinline__ Real pf_ref(Real zr) {
   return pf_r<Real>(cx_of(I), zr) * pf_r<Real>(cy_of(I), zr) * pf_r<Real>(cz_of(I), zr);
 }
 
+// Paired FP32 arithmetic (the f32x2 instructions of sm_100 and later): two
+// independent lanes per instruction.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  memcpy(&ra, &a, 8);
+  memcpy(&rb, &b, 8);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  memcpy(&d, &rd, 8);
+  return d;
+}
+
 }  // namespace lbm
