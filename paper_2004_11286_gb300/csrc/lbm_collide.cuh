@@ -84,6 +84,15 @@ constexpr int collide_min_blocks() {
 #define LBM_COLLIDE_BULK_MIN_M 3
 #endif
 
+// Population addresses as the node's own plus a per-plane byte offset from
+// the kernel parameters (1), or from the plane index times the grid size (0).
+// Measured on GB300: 256^3 shear layer FP32 4652 against 4430 MLUPS, 128^3
+// ternary mixture 3211 against 3048 (the same offsets for the gathers of the
+// side planes measured no faster: 4553).
+#ifndef LBM_PLANE_OFFSETS
+#define LBM_PLANE_OFFSETS 1
+#endif
+
 // Species counts from which the species update loops over the velocities at
 // run time rather than unrolled (see the species phase of collide_node).
 #ifndef LBM_SPECIES_LOOP_MIN_M
@@ -93,6 +102,13 @@ constexpr int collide_min_blocks() {
 // recomputed at every velocity (0).
 #ifndef LBM_SPECIES_AXIS_TABLES
 #define LBM_SPECIES_AXIS_TABLES 1
+#endif
+// FP32: the load phase's moment sums as pairs of lanes (species 2k, 2k + 1;
+// f, g) of the paired FP32 instructions (1), or one sum at a time (0).
+// Auto (2): where measured faster, M >= 3 or 16-bit storage (the FP32 M = 2
+// kernel spills with them: 256^3 shear layer 3909 against 4455 MLUPS).
+#ifndef LBM_PAIRED_MOMENTS
+#define LBM_PAIRED_MOMENTS 2
 #endif
 // FP32, M = 2 or 3: species 0 and 1 updated as one pair of lanes of the
 // paired FP32 instructions (1), or one species at a time (0).
@@ -156,12 +172,14 @@ __device__ __forceinline__ void issue_row_loads(const DevParams<Real>& p, const 
 // One node's collide + stream (thread threadIdx.x of the block; the block's
 // shared memory holds the stage and, with CL = 1, the network's tile).
 // WALL: bounce-back walls normal to x (register-load path only).
-template <int M, class Real, class Store, int PAR, int CL, int LD = 0, bool WALL = false>
+// POFF: the byte offsets of the population planes come from poff (the
+// kernel's parameter block), else they are computed from the grid size.
+template <int M, class Real, class Store, int PAR, int CL, int LD = 0, bool WALL = false, bool POFF = false>
 __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __restrict__ pops,
                                              Real* __restrict__ side, unsigned* __restrict__ err,
                                              const unsigned char* __restrict__ mlp_img,
                                              unsigned long long* __restrict__ mlp_stats, long long n_raw,
-                                             unsigned char* smem_raw) {
+                                             unsigned char* smem_raw, const long long* poff = nullptr) {
   constexpr int BS = collide_block<M, Real, CL, Store>();
   using SpT = StageSp<Real, Store>;
   // 16-bit storage: shifted deviations from the senders' equilibria (lbm_eqcodec.cuh)
@@ -184,6 +202,11 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
   MlpBlock<M, kMlpTiles<M, Real, Store>> mlp{smem_raw + collide_stage_bytes<M, Real, CL, Store>(), 0u, 0u};
   if constexpr (CL) mlp.begin_setup(mlp_img);
   const Nbr nb = make_nbr(p, n);
+  // Population k = L * 27 + slot of node `node`.
+  auto pop_at = [&](long long k, long long node) -> Store* {
+    if constexpr (POFF) return reinterpret_cast<Store*>(reinterpret_cast<char*>(pops + node) + poff[k]);
+    else return pops + (k * N + node);
+  };
 
   // a1 + a2: load (AA addressing), add the deferred terms of the previous
   // step, accumulate the moments of the deviations (the reference tables have
@@ -216,27 +239,67 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     }
   };
   auto species_val = [&](int a, int i, int cx) -> Real { return cell(a, i, cx); };
+  // FP32: species 2k and 2k + 1, and the f and g lattices, accumulate as
+  // the two lanes of paired FP32 instructions.
+  constexpr bool PA = std::is_same<Real, float>::value &&
+                      (LBM_PAIRED_MOMENTS == 2 ? (M >= 3 || sizeof(Store) == 2) : LBM_PAIRED_MOMENTS != 0);
+  constexpr int MP = PA ? M / 2 : 0;
+  float2 pr[MP > 0 ? MP : 1][4];         // (rho, j_x, j_y, j_z) of species 2k | 2k + 1
+  float2 pfg[4];                         // (rho, j) of f | (rho E, q) of g
+  if constexpr (PA) {
+#pragma unroll
+    for (int k = 0; k < MP; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pr[k][c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) pfg[c] = make_float2(0.f, 0.f);
+  }
+  auto acc2 = [](float2& a, float2 v, int c) {
+    if (c > 0) a = add2(a, v);
+    else if (c < 0) a = sub2(a, v);
+  };
   auto accumulate = [&](auto I_, const Real* v, Real fv, Real gv) {
     constexpr int i = decltype(I_)::value;
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+    if constexpr (PA) {
 #pragma unroll
-    for (int a = 0; a < M; ++a) {
-      rdev[a] += v[a];
-      if (cx) ja[a][0] += cx * v[a];
-      if (cy) ja[a][1] += cy * v[a];
-      if (cz) ja[a][2] += cz * v[a];
+      for (int k = 0; k < MP; ++k) {
+        const float2 vv = make_float2(v[2 * k], v[2 * k + 1]);
+        pr[k][0] = add2(pr[k][0], vv);
+        acc2(pr[k][1], vv, cx); acc2(pr[k][2], vv, cy); acc2(pr[k][3], vv, cz);
+      }
+      if constexpr (M % 2) {
+        rdev[M - 1] += v[M - 1];
+        if (cx) ja[M - 1][0] += cx * v[M - 1];
+        if (cy) ja[M - 1][1] += cy * v[M - 1];
+        if (cz) ja[M - 1][2] += cz * v[M - 1];
+      }
+      const float2 fg = make_float2(fv, gv);
+      pfg[0] = add2(pfg[0], fg);
+      acc2(pfg[1], fg, cx); acc2(pfg[2], fg, cy); acc2(pfg[3], fg, cz);
+    } else {
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        rdev[a] += v[a];
+        if (cx) ja[a][0] += cx * v[a];
+        if (cy) ja[a][1] += cy * v[a];
+        if (cz) ja[a][2] += cz * v[a];
+      }
+      rho_dev += fv;
+      if (cx) j[0] += cx * fv;
+      if (cy) j[1] += cy * fv;
+      if (cz) j[2] += cz * fv;
+      rhoE_dev += gv;
+      if (cx) q[0] += cx * gv;
+      if (cy) q[1] += cy * gv;
+      if (cz) q[2] += cz * gv;
     }
-    rho_dev += fv;
-    if (cx) { j[0] += cx * fv; S[0] += fv; }
-    if (cy) { j[1] += cy * fv; S[1] += fv; }
-    if (cz) { j[2] += cz * fv; S[2] += fv; }
+    if (cx) S[0] += fv;
+    if (cy) S[1] += fv;
+    if (cz) S[2] += fv;
     if (cx && cy) S[3] += (cx * cy) * fv;
     if (cx && cz) S[4] += (cx * cz) * fv;
     if (cy && cz) S[5] += (cy * cz) * fv;
-    rhoE_dev += gv;
-    if (cx) q[0] += cx * gv;
-    if (cy) q[1] += cy * gv;
-    if (cz) q[2] += cz * gv;
   };
   if constexpr (LD) {
     // The block is the row segment [x0, x0 + BS) of one grid row.  Every
@@ -284,17 +347,29 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       else if constexpr (i != 13) deferred_terms<Real, i, WALL>(side, N, nb, n, cf, cg);
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        const Real d = codec_load<Store, Real>(p, pops, (a * Q + slot) * N + node, a);
+        const Real d = codec_load<Store, Real>(p, pop_at(a * Q + slot, node), 0, a);
         if constexpr (EQ) v[a] += d; else v[a] = d;
         sps[(a * Q + i) * BS + tid] = v[a];
       }
-      Real fv = codec_load<Store, Real>(p, pops, (M * Q + slot) * N + node, M) + cf;
-      Real gv = codec_load<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1) + cg;
+      Real fv = codec_load<Store, Real>(p, pop_at(M * Q + slot, node), 0, M) + cf;
+      Real gv = codec_load<Store, Real>(p, pop_at((M + 1) * Q + slot, node), 0, M + 1) + cg;
       if constexpr (EQ) { fv += v[M]; gv += v[M + 1]; }
       sfg[i * BS + tid] = fv;
       sfg[(Q + i) * BS + tid] = gv;
       accumulate(I_, v, fv, gv);
     });
+  }
+
+  if constexpr (PA) {
+#pragma unroll
+    for (int k = 0; k < MP; ++k) {
+      rdev[2 * k] = pr[k][0].x; rdev[2 * k + 1] = pr[k][0].y;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { ja[2 * k][c] = pr[k][c + 1].x; ja[2 * k + 1][c] = pr[k][c + 1].y; }
+    }
+    rho_dev = pfg[0].x; rhoE_dev = pfg[0].y;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { j[c] = pfg[c + 1].x; q[c] = pfg[c + 1].y; }
   }
 
   // a3: coupling + thermodynamics
@@ -440,7 +515,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         s_f += e;
         const Real fv = cell(M, i, cx_of(i));
         const Real out = fv + om * (e - fv);
-        if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, EQ ? out - e : out);
+        if (active) codec_store<Store, Real>(p, pop_at(M * Q + slot, node), 0, M, EQ ? out - e : out);
       }
     });
     long long node; int slot;
@@ -448,7 +523,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     const Real fv = cell(M, 13, 0);
     const Real e13 = rho_dev - s_f;
     const Real out = fv + om * (e13 - fv);
-    if (active) codec_store<Store, Real>(p, pops, (M * Q + slot) * N + node, M, EQ ? out - e13 : out);
+    if (active) codec_store<Store, Real>(p, pop_at(M * Q + slot, node), 0, M, EQ ? out - e13 : out);
   }
 
   // a9: energy lattice.  With N = R^eq - rho E theta I, Eqs. (geq2mom),
@@ -533,29 +608,35 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     Real s_g = Real(0);
     const Nbr nbw = opaque(nb);
     const long long nw = kOpaqueStore<M, Store> ? opaque_idx(n) : n;
-    static_for<0, Q>([&](auto I_) {
-      constexpr int i = decltype(I_)::value;
-      if constexpr (i != 13) {
-        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        long long node; int slot;
-        aa_write_loc<WALL>(PAR, nbw, nw, i, node, slot);
-        const Real uc = dotc<Real, i>(th.u);
-        const Real cc = Real(0.5) * Real(c2_of(i));
-        const Real ucu = Gc * uc * uc * inv_theta;
-        const Real Ei = E0 + cc * rho + ucu;
-        const Real dEi = dE0 + cc * rho_dev + ucu;
-        const Real wx = cx ? w1 : w0, wy = cy ? w1 : w0, wz = cz ? w1 : w0;
-        const Real rx = cx ? r1 : r0, ry = cy ? r1 : r0, rz = cz ? r1 : r0;
-        const Real dx = cx ? d1 : d0, dy = cy ? d1 : d0, dz = cz ? d1 : d0;
-        const Real wi = wx * wy * wz;
-        const Real dwi = dx * wy * wz + rx * dy * wz + rx * ry * dz;
-        const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
-        s_g += e;
-        const Real gv = cell(M + 1, i, cx);
-        const Real out = gv + om * (e - gv) + wi * dotc<Real, i>(mvec);
-        if (active)
-          codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1,
-                                   EQ ? out - (e + wi * dotc<Real, i>(qt)) : out);
+    // The equilibrium deviation depends on c_i only through |c_ia| and
+    // (u . c_i)^2, so it is the same for i and opp(i): one evaluation per
+    // pair of opposite velocities; the flux term w_i c_i . m changes sign.
+    static_for<0, 13>([&](auto I_) {
+      constexpr int i = decltype(I_)::value, o = Q - 1 - i;
+      constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+      long long node_i, node_o; int slot_i, slot_o;
+      aa_write_loc<WALL>(PAR, nbw, nw, i, node_i, slot_i);
+      aa_write_loc<WALL>(PAR, nbw, nw, o, node_o, slot_o);
+      const Real uc = dotc<Real, i>(th.u);
+      const Real cc = Real(0.5) * Real(c2_of(i));
+      const Real ucu = Gc * uc * uc * inv_theta;
+      const Real Ei = E0 + cc * rho + ucu;
+      const Real dEi = dE0 + cc * rho_dev + ucu;
+      const Real wx = cx ? w1 : w0, wy = cy ? w1 : w0, wz = cz ? w1 : w0;
+      const Real rx = cx ? r1 : r0, ry = cy ? r1 : r0, rz = cz ? r1 : r0;
+      const Real dx = cx ? d1 : d0, dy = cy ? d1 : d0, dz = cz ? d1 : d0;
+      const Real wi = wx * wy * wz;
+      const Real dwi = dx * wy * wz + rx * dy * wz + rx * ry * dz;
+      const Real e = dwi * Ei + rx * ry * rz * dEi + BdotZ<Real, i>(dZ);
+      s_g += e + e;
+      const Real fl = wi * dotc<Real, i>(mvec);
+      const Real gvi = cell(M + 1, i, cx), gvo = cell(M + 1, o, -cx);
+      const Real out_i = gvi + om * (e - gvi) + fl;
+      const Real out_o = gvo + om * (e - gvo) - fl;
+      if (active) {
+        const Real sq = EQ ? wi * dotc<Real, i>(qt) : Real(0);
+        codec_store<Store, Real>(p, pop_at((M + 1) * Q + slot_i, node_i), 0, M + 1, EQ ? out_i - (e + sq) : out_i);
+        codec_store<Store, Real>(p, pop_at((M + 1) * Q + slot_o, node_o), 0, M + 1, EQ ? out_o - (e - sq) : out_o);
       }
     });
     long long node; int slot;
@@ -563,7 +644,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     const Real gv = cell(M + 1, 13, 0);
     const Real e13 = rhoE_dev - s_g;
     const Real out = gv + om * (e13 - gv);
-    if (active) codec_store<Store, Real>(p, pops, ((M + 1) * Q + slot) * N + node, M + 1, EQ ? out - e13 : out);
+    if (active) codec_store<Store, Real>(p, pop_at((M + 1) * Q + slot, node), 0, M + 1, EQ ? out - e13 : out);
   }
 
   // a7: species, Eqs. (SMlbm), (fstar1).  Equilibrium deviation
@@ -629,7 +710,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
         s_e[a] += e; s_F[a] += F;
         const Real kv = species_val(a, i, cx);
         const Real out = kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F;
-        if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
+        if (active) codec_store<Store, Real>(p, pop_at(a * Q + slot, node), 0, a, EQ ? out - e : out);
       }
     };
     if constexpr (M >= LBM_SPECIES_LOOP_MIN_M) {
@@ -723,8 +804,8 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
           const float2 out = fma2(bm2, F, fma2(bb2, sub2(e, kv), kv));
           const float2 st = EQ ? sub2(out, e) : out;
           if (active) {
-            codec_store<Store, Real>(p, pops, (0 * Q + slot) * N + node, 0, st.x);
-            codec_store<Store, Real>(p, pops, (1 * Q + slot) * N + node, 1, st.y);
+            codec_store<Store, Real>(p, pop_at(0 * Q + slot, node), 0, 0, st.x);
+            codec_store<Store, Real>(p, pop_at(1 * Q + slot, node), 0, 1, st.y);
           }
           if constexpr (M == 3) {
             const float F2 = K[2][0] * dif.x + K[2][1] * dif.y + K[2][2] * dif_2;
@@ -734,7 +815,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
             s_e[2] += e2; s_F[2] += F2;
             const float kv2 = species_val(2, i, cx - 1);
             const float out2 = kv2 + Real(2) * beta[2] * (e2 - kv2) + (beta[2] - Real(1)) * F2;
-            if (active) codec_store<Store, Real>(p, pops, (2 * Q + slot) * N + node, 2, EQ ? out2 - e2 : out2);
+            if (active) codec_store<Store, Real>(p, pop_at(2 * Q + slot, node), 0, 2, EQ ? out2 - e2 : out2);
           }
         }
       });
@@ -786,7 +867,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
             s_e[a] += e; s_F[a] += F;
             const Real kv = species_val(a, i, cx - 1);
             const Real out = kv + Real(2) * beta[a] * (e - kv) + (beta[a] - Real(1)) * F;
-            if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
+            if (active) codec_store<Store, Real>(p, pop_at(a * Q + slot, node), 0, a, EQ ? out - e : out);
           }
         }
       });
@@ -807,7 +888,7 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
       const Real e = th.rho_a_dev[a] - s_e[a];
       const Real kv = species_val(a, 13, 0);
       const Real out = kv + Real(2) * beta[a] * (e - kv) - (beta[a] - Real(1)) * s_F[a];
-      if (active) codec_store<Store, Real>(p, pops, (a * Q + slot) * N + node, a, EQ ? out - e : out);
+      if (active) codec_store<Store, Real>(p, pop_at(a * Q + slot, node), 0, a, EQ ? out - e : out);
     }
   }
   if constexpr (CL) mlp.teardown();
@@ -820,9 +901,10 @@ template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0, int W
 __global__ void __launch_bounds__(collide_block<M, Real, CL, Store>(), collide_min_blocks<M, Real, CL, Store>())
 collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
                unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
-               unsigned long long* __restrict__ mlp_stats) {
+               unsigned long long* __restrict__ mlp_stats, const __grid_constant__ PlaneOffsets po) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  collide_node<M, Real, Store, PAR, CL, LD, WALL != 0>(p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw);
+  collide_node<M, Real, Store, PAR, CL, LD, WALL != 0, LBM_PLANE_OFFSETS != 0>(p, pops, side, err, mlp_img, mlp_stats,
+                                                                                gtid(), smem_raw, po.off);
 }
 
 }  // namespace lbm

@@ -101,6 +101,13 @@ struct DevParams {
   Real Ur;
 };
 
+// Byte offsets k * N * sizeof(stored type) of the population planes
+// k = L * 27 + i (a kernel parameter: addresses then add a constant-bank
+// operand to the node's own address instead of multiplying by N).
+struct PlaneOffsets {
+  long long off[(MAXM + 2) * 27];
+};
+
 // ---------------------------------------------------------------------------
 // Product form, Sec. 2.4: triplets Psi_0, Psi_{+1}, Psi_{-1}.
 // ---------------------------------------------------------------------------

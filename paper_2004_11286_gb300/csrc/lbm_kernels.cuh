@@ -253,12 +253,14 @@ struct Launch {
                            (int)smem);
       attr = true;
     }
+    PlaneOffsets po;
+    for (int k = 0; k < (M + 2) * Q; ++k) po.off[k] = (long long)k * c.N * (long long)sizeof(Store);
     if (parity == 0)
       collide_kernel<M, Real, Store, 0, CL, LD, WALL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
-          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
+          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats, po);
     else
       collide_kernel<M, Real, Store, 1, CL, LD, WALL><<<grid_for(c.N, BS), BS, smem, c.stream>>>(
-          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats);
+          P(c), (Store*)c.pops, side, c.err, c.mlp_img, c.mlp_stats, po);
   }
   // Bulk row loads where the blocks are whole row segments and the stage
   // holds the stored type (FP64, FP32).
