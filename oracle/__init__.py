@@ -10,5 +10,5 @@ CUDA path; it takes its inputs as plain NumPy arrays.
 from .lbm_oracle import (  # noqa: F401
     C, OPP, Q, Params, psi_product, g_ansatz, iso_derivative, stream,
     moments, node_state, sm_momenta, collide, step, run, init_populations,
-    macroscopic, collide_patch_center, conserved_sums,
+    macroscopic, collide_patch_center, conserved_sums, Frame, stream_frame, XREF,
 )

@@ -44,6 +44,18 @@ the design notes):
     wall-normal component of a momentum-like field).  The paper leaves both
     the derivative and the wall treatment of the three-dimensional model
     unstated.
+  * the opposed-jets boundary set of Sec. 4.3 (``frame``, class Frame): a
+    layer of nodes outside the x and y faces holds, after every collision,
+    post-collision populations that then stream into the domain.  On the x
+    faces, rows inside the nozzles hold the complete equilibrium of the
+    inlet state (the incoming populations replaced by equilibria); the other
+    rows are free-slip walls, the mirror image of the boundary node with the
+    x velocity reflected (specular reflection halfway between the nodes).
+    On the y faces (the outlets) the outside node is a copy of the boundary
+    node (zero normal derivative).  An outside node beyond both faces takes
+    the x-face rule of the boundary row it is next to.  The isotropic
+    derivative reads an outside node as the value of its nearest boundary
+    node, negated for Phi_x beyond a free-slip wall.
 """
 
 from __future__ import annotations
@@ -86,6 +98,7 @@ class Params:
     coupling: str = "strong"
     slaved: int = -1
     walls_x: bool = False           # bounce-back walls at x = -1/2 and x = nx - 1/2
+    frame: Optional["Frame"] = None  # opposed-jets boundary set (Sec. 4.3)
     # temperature-dependent specific heats (Sec. 3.1): C-bar_{a,v}(T) / R_U =
     # sum_k cv_poly[a, k] T^k; None: the constants cv_molar (T0 = 0 either way)
     cv_poly: Optional[np.ndarray] = None
@@ -111,6 +124,7 @@ class Params:
         if self.slaved < 0:
             self.slaved = self.M - 1
         assert self.coupling in ("strong", "weak")
+        assert not (self.walls_x and self.frame is not None), "walls_x and frame exclude each other"
         if self.cv_poly is not None:
             self.cv_poly = np.asarray(self.cv_poly, dtype=np.float64).reshape(self.M, -1)
 
@@ -224,6 +238,90 @@ def g_ansatz(theta, M0, m, Mt):
 # Lattice operators
 # ----------------------------------------------------------------------------
 
+XREF = np.array([int(np.where((C == C[i] * np.array([-1, 1, 1])).all(axis=1))[0][0]) for i in range(Q)])
+
+
+@dataclass
+class Frame:
+    """Boundary set of the opposed jets (Sec. 4.3; the readings are in the
+    module docstring).  y0, y1: the interior rows [y0, y1) of both x faces that
+    are nozzles; inlet: the complete populations (S, 27) entering through
+    the nozzle at x = -1 (inlet[0]) and at x = nx (inlet[1]).  x_faces /
+    y_faces False leave that pair of faces periodic."""
+    y0: int
+    y1: int
+    inlet: tuple = ()
+    x_faces: bool = True
+    y_faces: bool = True
+
+
+def _frame_rows(ny: int, fr: Frame):
+    """For each row yp of the padded grid (yp = y + 1), the interior row it
+    takes its values from: the nearest one beyond outlets, the wrapped one
+    beyond periodic y faces."""
+    yp = np.arange(ny + 2) - 1
+    return np.clip(yp, 0, ny - 1) if fr.y_faces else yp % ny
+
+
+def _frame_pad_pops(post, fr: Frame):
+    """Post-collision populations (S, 27, nz, ny, nx) with one layer of outside
+    nodes on the x and y faces, (S, 27, nz, ny + 2, nx + 2)."""
+    S, _, nz, ny, nx = post.shape
+    pad = np.empty((S, Q, nz, ny + 2, nx + 2))
+    pad[..., 1:-1, 1:-1] = post
+    if fr.y_faces:                              # outlets: copies of the boundary rows
+        pad[..., 0, 1:-1] = post[..., 0, :]
+        pad[..., -1, 1:-1] = post[..., -1, :]
+    else:
+        pad[..., 0, 1:-1] = post[..., -1, :]
+        pad[..., -1, 1:-1] = post[..., 0, :]
+    if not fr.x_faces:
+        pad[..., 0] = pad[..., nx]
+        pad[..., -1] = pad[..., 1]
+        return pad
+    rows = _frame_rows(ny, fr)
+    for yp in range(ny + 2):
+        yc = int(rows[yp])
+        for side, xo, xb in ((0, 0, 0), (1, nx + 1, nx - 1)):
+            if fr.y0 <= yc < fr.y1:             # nozzle: the inlet equilibrium
+                pad[:, :, :, yp, xo] = np.asarray(fr.inlet[side])[:, :, None]
+            else:                               # free-slip wall: x velocity reflected
+                pad[:, :, :, yp, xo] = post[:, XREF][:, :, :, yc, xb]
+    return pad
+
+
+def _frame_pad_field(phi, fr: Frame, odd_x: bool = False):
+    """A field (..., nz, ny, nx) with one layer of outside nodes: the nearest
+    boundary node's value (wrapped on periodic faces), negated beyond a
+    free-slip wall for a field odd in x."""
+    ny, nx = phi.shape[-2], phi.shape[-1]
+    pad = np.empty(phi.shape[:-2] + (ny + 2, nx + 2))
+    rows = _frame_rows(ny, fr)
+    inner = phi[..., rows, :]                   # (..., ny + 2, nx)
+    pad[..., 1:-1] = inner
+    if not fr.x_faces:
+        pad[..., 0] = inner[..., -1]
+        pad[..., -1] = inner[..., 0]
+        return pad
+    nozzle = (rows >= fr.y0) & (rows < fr.y1)
+    sgn = np.where(nozzle, 1.0, -1.0) if odd_x else np.ones(ny + 2)
+    pad[..., 0] = sgn * inner[..., 0]
+    pad[..., -1] = sgn * inner[..., -1]
+    return pad
+
+
+def stream_frame(post, fr: Frame):
+    """Propagation with the opposed-jets boundary set: every population moves
+    from x - c_i to x, those from outside the domain taken from the outside
+    layer of _frame_pad_pops."""
+    pad = _frame_pad_pops(post, fr)
+    out = np.empty_like(post)
+    for i in range(Q):
+        sh = np.roll(pad[:, i], shift=(int(C[i, 2]), int(C[i, 1]), int(C[i, 0])), axis=(-3, -2, -1))
+        out[:, i] = sh[..., 1:-1, 1:-1]
+    return out
+
+
 def _shift(phi, c, walls_x: bool = False, odd_x: bool = False):
     """phi(x + c); phi has shape (..., nz, ny, nx).  Periodic in every
     direction, or, with walls_x, mirrored across the two x walls: the node
@@ -242,9 +340,17 @@ def _shift(phi, c, walls_x: bool = False, odd_x: bool = False):
     return out
 
 
-def iso_derivative(phi, alpha: int, walls_x: bool = False, odd_x: bool = False):
+def iso_derivative(phi, alpha: int, walls_x: bool = False, odd_x: bool = False, frame: Optional[Frame] = None):
     """Second-order isotropic lattice derivative of Sec. 4.1 (reading):
     d_alpha phi(x) = 3 sum_i w_i c_{i alpha} phi(x + c_i)."""
+    if frame is not None:
+        pad = _frame_pad_field(phi, frame, odd_x)
+        acc = np.zeros_like(pad, dtype=np.float64)
+        for i in range(Q):
+            if C[i, alpha] != 0:
+                acc = acc + _W_ISO[i] * C[i, alpha] * np.roll(pad, shift=(-int(C[i, 2]), -int(C[i, 1]), -int(C[i, 0])),
+                                                              axis=(-3, -2, -1))
+        return 3.0 * acc[..., 1:-1, 1:-1]
     acc = np.zeros_like(phi, dtype=np.float64)
     for i in range(Q):
         if C[i, alpha] != 0:
@@ -439,12 +545,12 @@ def collide(pops, prm: Params, return_aux: bool = False):
     omega, omega1 = st["omega"], st["omega1"]
 
     # --- non-local fields (Sec. 4.1 derivatives of time-t moments) ---------
-    wx = prm.walls_x
+    wx, fr = prm.walls_x, prm.frame
     Phi = [j[a] * (1.0 - 3.0 * R * T) - rho * u[a] ** 3 for a in range(3)]
     c_om = 1.0 / omega - 0.5
-    Gs = [c_om * iso_derivative(Phi[a], a, wx, odd_x=(a == 0)) for a in range(3)]
-    Xc = np.stack([-iso_derivative(Gs[a], a, wx) for a in range(3)])  # Eq. (Xalpha)
-    gradY = np.stack([np.stack([iso_derivative(st["Y"][a], b, wx) for b in range(3)])
+    Gs = [c_om * iso_derivative(Phi[a], a, wx, odd_x=(a == 0), frame=fr) for a in range(3)]
+    Xc = np.stack([-iso_derivative(Gs[a], a, wx, frame=fr) for a in range(3)])  # Eq. (Xalpha)
+    gradY = np.stack([np.stack([iso_derivative(st["Y"][a], b, wx, frame=fr) for b in range(3)])
                       for a in range(M)])                              # (M, 3, ...)
 
     # --- species, Eqs. (tauab), (tau), beta_a, (SMlbm), (fstar1) ------------
@@ -534,6 +640,8 @@ def collide(pops, prm: Params, return_aux: bool = False):
 
 def step(pops, prm: Params):
     """One time step: collide at every node, then stream (Eqs. SMlbm, fwithcorrection, g)."""
+    if prm.frame is not None:
+        return stream_frame(collide(pops, prm), prm.frame)
     return stream(collide(pops, prm), prm.walls_x)
 
 

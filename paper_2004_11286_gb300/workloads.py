@@ -221,6 +221,79 @@ def loschmidt_tube(case: str = "1T", L: int = 96, width: float = 3.0, floor: flo
     return Workload(f"loschmidt_{case}", mm, cv, D, mu, lam, X, np.zeros((3, 1, 1, L)), T, P, steps)
 
 
+# Opposed jets of Sec. 4.3: H2, N2, O2, H2O; the jet compositions as printed
+# (left, right).  Binary diffusivities: ratios of tabulated near-ambient
+# values for these pairs (H2-N2 0.78, H2-O2 0.81, H2-H2O 0.92, N2-O2 0.21,
+# N2-H2O 0.25, O2-H2O 0.25 cm^2/s), scaled in the recipe.
+JETS_SPECIES = ("H2", "N2", "O2", "H2O")
+JETS_MASS = np.array([2.016, 28.014, 31.998, 18.015])
+JETS_CV = np.array([2.5, 2.5, 2.5, 3.0])
+JETS_X = (np.array([0.1, 0.85, 0.0, 0.05]), np.array([0.0, 0.90, 0.1, 0.0]))
+JETS_D_RATIO = np.array([[0.0, 0.78, 0.81, 0.92],
+                         [0.78, 0.0, 0.21, 0.25],
+                         [0.81, 0.21, 0.0, 0.25],
+                         [0.92, 0.25, 0.25, 0.0]])
+
+
+@dataclass
+class JetInlets:
+    """The two nozzles of the opposed-jets frame: interior rows [y0, y1) of
+    both x faces, and for the nozzle at x = -1 (index 0) and at x = nx (1) the
+    mole fractions, x velocity, temperature and pressure."""
+    y0: int
+    y1: int
+    X: np.ndarray          # (2, M)
+    u: np.ndarray          # (2,)
+    T: np.ndarray          # (2,)
+    P: np.ndarray          # (2,)
+
+
+def opposed_jets(nx: int = 200, ny: int = 400, nz: int = 1, U: float = 0.01, floor: float = 0.01,
+                 D_h2_n2: float = 0.02, mu_factor: float = 0.5, nozzle=(0.1, 0.9), steps: int = 40000):
+    """Planar opposed jets of Sec. 4.3 on an nx x ny x nz interior (the paper:
+    200 x 400 x 1).  Nozzles over the rows [0.1 ny, 0.9 ny) of both x faces;
+    the jets' mole fractions as printed, floored at `floor` and renormalised
+    (a species left at zero drives the method unstable, as for the Loschmidt
+    tube); the left jet at x velocity U, the right one at the speed that
+    gives equal momentum flux rho U^2 at the common T and P.  Binary
+    diffusivities in the tabulated ratios with D(H2, N2) = D_h2_n2; species
+    viscosities mu_factor * P0.  The interior starts at rest with the left
+    composition for x < nx/2 and the right one beyond (a tanh step of 4
+    cells).  Returns (Workload, JetInlets)."""
+    XL, XR = (np.maximum(floor, v) for v in JETS_X)
+    XL, XR = XL / XL.sum(), XR / XR.sum()
+    mm, cv = JETS_MASS.copy(), JETS_CV.copy()
+    M = 4
+    T0 = T_AMBIENT
+    P0 = _p0(0.5 * (XL + XR), mm, T0)
+    mL, mR = float(XL @ mm), float(XR @ mm)
+    UR = U * np.sqrt(mL / mR)                          # rho ~ m at equal T and P
+    D = JETS_D_RATIO * (D_h2_n2 / JETS_D_RATIO[0, 1])
+    mu, lam = _transport(mm, cv, P0, mu_factor)
+    x = np.arange(nx) + 0.5
+    s = 0.5 * (1.0 + np.tanh((x - 0.5 * nx) / 4.0))   # 0 left, 1 right
+    X = np.empty((M, nz, ny, nx))
+    for a in range(M):
+        X[a] = (XL[a] + (XR[a] - XL[a]) * s)[None, None, :]
+    u = np.zeros((3, nz, ny, nx))
+    T = np.full((nz, ny, nx), T0)
+    P = np.full((nz, ny, nx), P0)
+    wl = Workload("opposed_jets", mm, cv, D, mu, lam, X, u, T, P, steps)
+    y0, y1 = int(round(nozzle[0] * ny)), int(round(nozzle[1] * ny))
+    inl = JetInlets(y0, y1, np.stack([XL, XR]), np.array([U, -UR]), np.array([T0, T0]), np.array([P0, P0]))
+    return wl, inl
+
+
+def with_frame(a):
+    """A field (..., nz, ny, nx) on the grid with the one-node frame of the
+    opposed-jets boundary set, (..., nz, ny + 2, nx + 2): the frame nodes
+    take the nearest interior value (they are overwritten by the boundary
+    rules before any population leaves them)."""
+    a = np.asarray(a)
+    pad = [(0, 0)] * (a.ndim - 2) + [(1, 1), (1, 1)]
+    return np.pad(a, pad, mode="edge")
+
+
 def khi_n2_h2o(shape=(200, 800, 800), reynolds: float = 11963.46, mach_r: float = 0.2, schmidt: float = 0.6,
                width: float = 0.0, steps: int = 0) -> Workload:
     """The three-dimensional Kelvin-Helmholtz instability of Sec. 4.5
