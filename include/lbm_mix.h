@@ -60,7 +60,9 @@ typedef enum {
   LBM_ERR_STATE = 6         /* call out of order (e.g. step before init) */
 } lbm_status;
 
-enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+/* Boundary types of the six faces (lbm_mix_params.bc).  LBM_BC_JET and
+ * LBM_BC_OUTLET make the opposed-jets boundary set of Sec. 4.3; see bc. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1, LBM_BC_JET = 2, LBM_BC_OUTLET = 3 };
 /* Precision of the populations in memory and of the arithmetic:
  *   FP64, FP32: stored as deviations from one reference rest state, arithmetic
  *     in the same type;
@@ -99,9 +101,29 @@ typedef struct {
                                  LBM_BC_BOUNCEBACK on both x faces with y and z
                                  periodic (the closed tube of Sec. 4.2: halfway
                                  bounce-back of every lattice; gradients mirror
-                                 the field across the wall, odd for Phi_x).
+                                 the field across the wall, odd for Phi_x), or
+                                 LBM_BC_JET on both x faces, LBM_BC_OUTLET on both
+                                 y faces and z periodic: the opposed jets of
+                                 Sec. 4.3.  Then the outermost x and y layers of
+                                 the grid are a frame of outside nodes that take
+                                 no collision: after every collision they hold
+                                 the post-collision populations that stream into
+                                 the domain.  On the x faces, rows jet_y0 <= y <
+                                 jet_y1 are nozzles (the complete equilibrium of
+                                 the inlet state, Eqs. 27eq, feq, gieq), the other
+                                 rows free-slip walls (the boundary node's mirror
+                                 image, x velocity reflected); on the y faces a
+                                 copy of the boundary node (zero normal
+                                 derivative); a corner takes the x-face rule of
+                                 its nearest boundary row.  Gradients read a
+                                 frame node as its nearest boundary node, with
+                                 Phi_x negated beyond a free-slip wall.  Frame
+                                 nodes carry no state of their own (their
+                                 observables and conservation sums are not
+                                 meaningful).  FP64 and FP32 storage, exact
+                                 closure, constant heats only.
                                  Other combinations: LBM_ERR_UNSUPPORTED; walls
-                                 with LBM_CLOSURE_MLP or in a batch likewise. */
+                                 or jets with LBM_CLOSURE_MLP or in a batch likewise. */
   int slaved_species;         /* strong coupling: slaved index, -1 -> M-1 (Sec. 3.5.2) */
   int precision;              /* LBM_PREC_* */
   int coupling;               /* LBM_COUPLE_* */
@@ -125,6 +147,11 @@ typedef struct {
                                  reached.  FP64 and FP32 storage; not with walls,
                                  LBM_CLOSURE_MLP or in a batch (LBM_ERR_UNSUPPORTED). */
   int cv_terms;               /* 1..3 coefficients per species with cv_poly */
+  /* LBM_BC_JET: the two nozzles, index 0 on the x = 0 face, 1 on x = nx - 1. */
+  const double* jet_X;        /* [2][M] inlet mole fractions (each row sums to 1) */
+  double jet_u[2];            /* inlet x velocities (into the domain: [0] > 0, [1] < 0) */
+  double jet_T[2], jet_P[2];  /* inlet temperatures and pressures (> 0) */
+  int jet_y0, jet_y1;         /* nozzle rows [jet_y0, jet_y1), 1 <= jet_y0 <= jet_y1 <= ny - 1 */
 } lbm_mix_params;
 
 typedef struct lbm_mix* lbm_mix_t;

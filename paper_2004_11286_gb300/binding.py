@@ -39,6 +39,8 @@ class lbm_mix_params(ct.Structure):
         ("fp64_cond_bound", ct.c_double),
         ("closure_residual_bound", ct.c_double),
         ("cv_poly", _DP), ("cv_terms", ct.c_int),
+        ("jet_X", _DP), ("jet_u", ct.c_double * 2), ("jet_T", ct.c_double * 2), ("jet_P", ct.c_double * 2),
+        ("jet_y0", ct.c_int), ("jet_y1", ct.c_int),
     ]
 
 
@@ -129,10 +131,13 @@ def _dp(a: Optional[np.ndarray]):
 def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), precision: str = "fp32",
                 coupling: str = "strong", slaved: int = -1, omega_fixed: float = 0.0, omega1_fixed: float = 0.0,
                 R_U: float = 1.0, fp64_cond_bound: float = 0.0, closure: str = "exact",
-                closure_bound: float = 0.0, walls_x: bool = False, cv_poly=None):
+                closure_bound: float = 0.0, walls_x: bool = False, cv_poly=None, jets=None):
     """(lbm_mix_params, keepalive arrays) for one nz x ny x nx domain, periodic,
     or with bounce-back walls on both x faces (walls_x); cv_poly (M, K <= 3):
-    temperature-dependent molar heats C-bar_{a,v}(T)/R_U = sum_k cv_poly[a, k] T^k."""
+    temperature-dependent molar heats C-bar_{a,v}(T)/R_U = sum_k cv_poly[a, k] T^k.
+    jets: the opposed-jets boundary set (LBM_BC_JET on the x faces,
+    LBM_BC_OUTLET on the y faces); an object with y0, y1 (nozzle rows of the
+    grid, frame included), X (2, M), u, T, P (2,)."""
     M = int(len(molar_mass))
     nz, ny, nx = (int(v) for v in shape)
     keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in (molar_mass, cv_molar, D)]
@@ -148,6 +153,17 @@ def make_params(molar_mass, cv_molar, D, mu=None, lam=None, shape=(1, 1, 1), pre
     p.nx, p.ny, p.nz = nx, ny, nz
     for k in range(6):
         p.bc[k] = 1 if (walls_x and k < 2) else 0
+    if jets is not None:
+        for k in range(4):
+            p.bc[k] = 2 if k < 2 else 3
+        jx = np.ascontiguousarray(np.asarray(jets.X, dtype=np.float64).reshape(2, M))
+        keep.append(jx)
+        p.jet_X = _dp(jx)
+        for k in range(2):
+            p.jet_u[k], p.jet_T[k], p.jet_P[k] = float(jets.u[k]), float(jets.T[k]), float(jets.P[k])
+        p.jet_y0, p.jet_y1 = int(jets.y0), int(jets.y1)
+    else:
+        p.jet_X = _dp(None)
     p.slaved_species = int(slaved)
     p.precision = PREC[precision]
     p.coupling = COUPLING[coupling]
@@ -177,7 +193,7 @@ class LbmMix:
                  precision: str = "fp32", coupling: str = "strong", slaved: int = -1,
                  omega_fixed: float = 0.0, omega1_fixed: float = 0.0, R_U: float = 1.0,
                  fp64_cond_bound: float = 0.0, closure: str = "exact", closure_bound: float = 0.0,
-                 walls_x: bool = False, device=None, stream=None, cv_poly=None):
+                 walls_x: bool = False, device=None, stream=None, cv_poly=None, jets=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -190,7 +206,7 @@ class LbmMix:
                                     coupling=coupling, slaved=slaved, omega_fixed=omega_fixed,
                                     omega1_fixed=omega1_fixed, R_U=R_U, fp64_cond_bound=fp64_cond_bound,
                                     closure=closure, closure_bound=closure_bound, walls_x=walls_x,
-                                    cv_poly=cv_poly)
+                                    cv_poly=cv_poly, jets=jets)
         self._owned = True
         self.precision = precision
         with torch.cuda.device(self.device):

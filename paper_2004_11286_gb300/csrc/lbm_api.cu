@@ -48,6 +48,7 @@ template <class Real>
 void fill_params(lbm::DevParams<Real>& d, const lbm::DevParams<double>& s) {
   d.N = s.N; d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.M = s.M; d.slaved = s.slaved; d.weak = s.weak;
   d.wall_x = s.wall_x;
+  d.frame = s.frame; d.jet_y0 = s.jet_y0; d.jet_y1 = s.jet_y1;
   d.omega_is_fixed = s.omega_is_fixed; d.omega1_is_fixed = s.omega1_is_fixed;
   d.omega_fixed = (Real)s.omega_fixed; d.omega1_fixed = (Real)s.omega1_fixed;
   d.R_U = (Real)s.R_U; d.cond_bound = (Real)s.cond_bound; d.closure_bound = (Real)s.closure_bound;
@@ -186,6 +187,7 @@ struct lbm_mix {
   lbm::DevParams<float> p32{};
   double base[(lbm::MAXM + 2) * 27] = {};   // host copy of the reference rest equilibria
   double* d_base = nullptr;
+  double* d_jet = nullptr;     // opposed-jets frame: inlet equilibria (KernelSet::jet_table)
   bool has_reference = false;
   bool fixed_reference = false;    // set by lbm_mix_set_reference: init_fields keeps it
   void* pops = nullptr;
@@ -229,6 +231,7 @@ struct lbm_mix {
     c.N = N; c.stream = stream; c.pops = pops; c.side = scratch; c.err = d_err;
     c.partials = d_partials; c.p64 = &p64; c.p32 = &p32; c.base = d_base; c.ev = nullptr;
     c.closure = closure; c.mlp_img = d_img; c.mlp_stats = d_stats;
+    c.jet = d_jet;
     return c;
   }
   lbm_status fail(lbm_status s, const std::string& m) { err = m; return s; }
@@ -592,14 +595,35 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return bad("grids must have fewer than 2^31 nodes");
   if (!(p->R_U > 0.0)) return bad("R_U must be > 0");
   for (int s = 0; s < 6; ++s)
-    if (p->bc[s] != LBM_BC_PERIODIC && p->bc[s] != LBM_BC_BOUNCEBACK) return bad("unknown boundary type");
-  // Built: periodic everywhere, or bounce-back walls on both x faces with
-  // periodic y and z (the closed tube).
+    if (p->bc[s] < LBM_BC_PERIODIC || p->bc[s] > LBM_BC_OUTLET) return bad("unknown boundary type");
+  // Built: periodic everywhere; bounce-back walls on both x faces with
+  // periodic y and z (the closed tube); the opposed-jets frame (jets on both
+  // x faces, outlets on both y faces, periodic z).
   const bool walls = p->bc[0] == LBM_BC_BOUNCEBACK;
+  const bool jets = p->bc[0] == LBM_BC_JET;
   for (int s = 0; s < 6; ++s) {
-    const int want = (s < 2 && walls) ? LBM_BC_BOUNCEBACK : LBM_BC_PERIODIC;
+    const int want = (s < 2 && walls) ? LBM_BC_BOUNCEBACK
+                   : (jets && s < 2) ? LBM_BC_JET : (jets && s < 4) ? LBM_BC_OUTLET : LBM_BC_PERIODIC;
     if (p->bc[s] != want) {
-      g_create_error = "boundaries built: all periodic, or bounce-back on both x faces with y, z periodic";
+      g_create_error = "boundaries built: all periodic; bounce-back on both x faces with y, z periodic; "
+                       "jets on both x faces with outlets on both y faces and z periodic";
+      return LBM_ERR_UNSUPPORTED;
+    }
+  }
+  if (jets) {
+    if (p->nx < 3 || p->ny < 3) return bad("the jets frame needs nx, ny >= 3");
+    if (!(p->jet_y0 >= 1 && p->jet_y0 <= p->jet_y1 && p->jet_y1 <= p->ny - 1))
+      return bad("nozzle rows need 1 <= jet_y0 <= jet_y1 <= ny - 1");
+    if (!p->jet_X) return bad("jet_X is required with LBM_BC_JET");
+    for (int k = 0; k < 2; ++k) {
+      if (!(p->jet_T[k] > 0.0) || !(p->jet_P[k] > 0.0)) return bad("inlet T and P must be > 0");
+      if (!std::isfinite(p->jet_u[k])) return bad("inlet velocity must be finite");
+      for (int a = 0; a < M; ++a)
+        if (!(p->jet_X[k * M + a] >= 0.0)) return bad("inlet mole fractions must be >= 0");
+    }
+    if (!(p->precision == LBM_PREC_FP64 || p->precision == LBM_PREC_FP32) || p->closure == LBM_CLOSURE_MLP ||
+        p->cv_poly) {
+      g_create_error = "the jets frame runs with FP64 or FP32 storage, the exact closure and constant heats";
       return LBM_ERR_UNSUPPORTED;
     }
   }
@@ -672,6 +696,8 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
   d.N = h->N; d.nx = p->nx; d.ny = p->ny; d.nz = p->nz; d.M = M; d.slaved = slaved;
   d.weak = p->coupling == LBM_COUPLE_WEAK;
   d.wall_x = walls ? 1 : 0;
+  d.frame = jets ? 1 : 0;
+  d.jet_y0 = jets ? p->jet_y0 : 0; d.jet_y1 = jets ? p->jet_y1 : 0;
   d.omega_is_fixed = p->omega_fixed > 0.0; d.omega1_is_fixed = p->omega1_fixed > 0.0;
   d.omega_fixed = p->omega_fixed; d.omega1_fixed = p->omega1_fixed; d.R_U = p->R_U;
   d.cond_bound = p->fp64_cond_bound > 0.0 ? p->fp64_cond_bound : 1e3;
@@ -739,6 +765,27 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream);
   }
   if (e == cudaSuccess) e = ks->mlp_pack(h->ctx(), h->d_w, h->d_img);
+  if (e == cudaSuccess && jets) {
+    // the complete equilibria of the two inlet states (the library's own FP64
+    // initial-state kernel on a two-node grid)
+    const int S = M + 2;
+    const size_t n_out = (size_t)S * 27 * 2, n_zero = (size_t)S * 27, n_in = (size_t)M * 2 + 6 + 2 + 2;
+    std::vector<double> in(n_in, 0.0);
+    for (int k = 0; k < 2; ++k) {
+      for (int a = 0; a < M; ++a) in[(size_t)a * 2 + k] = p->jet_X[k * M + a];
+      in[(size_t)M * 2 + 0 * 2 + k] = p->jet_u[k];
+      in[(size_t)M * 2 + 6 + k] = p->jet_T[k];
+      in[(size_t)M * 2 + 8 + k] = p->jet_P[k];
+    }
+    e = cudaMalloc(&h->d_jet, (n_out + n_zero + n_in) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_jet, 0, (n_out + n_zero) * sizeof(double), h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_jet + n_out + n_zero, in.data(), n_in * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess) e = ks->jet_table(h->ctx(), h->d_jet);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);      // `in` leaves scope
+    h->launches += 1;
+  }
   if (e != cudaSuccess) {
     g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
     if (h->d_err) cudaFree(h->d_err);
@@ -748,6 +795,7 @@ lbm_status lbm_mix_create(const lbm_mix_params* p, void* cuda_stream, lbm_mix_t*
     if (h->d_w) cudaFree(h->d_w);
     if (h->d_img) cudaFree(h->d_img);
     if (h->d_stats) cudaFree(h->d_stats);
+    if (h->d_jet) cudaFree(h->d_jet);
     delete h;
     return LBM_ERR_CUDA;
   }
@@ -836,7 +884,7 @@ lbm_status lbm_mix_step(lbm_mix_t h, int nsteps) {
     lbm_status st = h->cuda(h->ks->step(c, (int)(h->steps & 1)), "step kernels");
     if (st != LBM_OK) return st;
     h->steps += 1;
-    h->launches += h->ks->launches_per_step;
+    h->launches += h->ks->launches_per_step + (h->p64.frame ? 4 : 0);
   }
   return LBM_OK;
 }
@@ -1434,6 +1482,7 @@ lbm_status lbm_mix_destroy(lbm_mix_t h) {
   cudaFree(h->d_err); cudaFree(h->d_partials); cudaFree(h->d_sums); cudaFree(h->d_base);
   cudaFree(h->d_w); cudaFree(h->d_img); cudaFree(h->d_stats);
   if (h->z_base) cudaFree(h->z_base);
+  if (h->d_jet) cudaFree(h->d_jet);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return LBM_OK;

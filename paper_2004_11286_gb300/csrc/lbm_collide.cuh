@@ -174,7 +174,10 @@ __device__ __forceinline__ void issue_row_loads(const DevParams<Real>& p, const 
 // WALL: bounce-back walls normal to x (register-load path only).
 // POFF: the byte offsets of the population planes come from poff (the
 // kernel's parameter block), else they are computed from the grid size.
-template <int M, class Real, class Store, int PAR, int CL, int LD = 0, bool WALL = false, bool POFF = false>
+// FRAME: the outermost x and y layers are the opposed-jets frame, whose nodes
+// take no collision (lbm_frame.cuh).
+template <int M, class Real, class Store, int PAR, int CL, int LD = 0, bool WALL = false, bool POFF = false,
+          bool FRAME = false>
 __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __restrict__ pops,
                                              Real* __restrict__ side, unsigned* __restrict__ err,
                                              const unsigned char* __restrict__ mlp_img,
@@ -199,6 +202,10 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
     if (!active) return;
   }
   const long long n = active ? n_raw : N - 1;
+  if constexpr (FRAME && !CL) {
+    const long long x = n % p.nx, y = (n / p.nx) % p.ny;
+    if (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1) return;
+  }
   MlpBlock<M, kMlpTiles<M, Real, Store>> mlp{smem_raw + collide_stage_bytes<M, Real, CL, Store>(), 0u, 0u};
   if constexpr (CL) mlp.begin_setup(mlp_img);
   const Nbr nb = make_nbr(p, n);
@@ -896,15 +903,16 @@ __device__ __forceinline__ void collide_node(const DevParams<Real>& p, Store* __
 
 // LD = 1: bulk row loads; needs Store == Real, nx a multiple of the block
 // size and a grid whose blocks are whole row segments (checked by the host).
-// WALL = 1: bounce-back walls normal to x (with LD = 0).
+// WALL = 1: bounce-back walls normal to x (with LD = 0); WALL = 2: the
+// opposed-jets frame (with LD = 0).
 template <int M, class Real, class Store, int PAR, int CL = 0, int LD = 0, int WALL = 0>
 __global__ void __launch_bounds__(collide_block<M, Real, CL, Store>(), collide_min_blocks<M, Real, CL, Store>())
 collide_kernel(const __grid_constant__ DevParams<Real> p, Store* __restrict__ pops, Real* __restrict__ side,
                unsigned* __restrict__ err, const unsigned char* __restrict__ mlp_img,
                unsigned long long* __restrict__ mlp_stats, const __grid_constant__ PlaneOffsets po) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  collide_node<M, Real, Store, PAR, CL, LD, WALL != 0, LBM_PLANE_OFFSETS != 0>(p, pops, side, err, mlp_img, mlp_stats,
-                                                                                gtid(), smem_raw, po.off);
+  collide_node<M, Real, Store, PAR, CL, LD, WALL == 1, LBM_PLANE_OFFSETS != 0, WALL == 2>(
+      p, pops, side, err, mlp_img, mlp_stats, gtid(), smem_raw, po.off);
 }
 
 }  // namespace lbm

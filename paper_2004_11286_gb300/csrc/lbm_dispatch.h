@@ -22,6 +22,7 @@ struct LaunchCtx {
   int closure;                          // 1: learned closure in the step
   const unsigned char* mlp_img;         // device bf16/FP32 image of the network
   unsigned long long* mlp_stats;        // [accepted, fallback] node counters
+  const double* jet;                    // opposed-jets frame: inlet equilibria [(L * 27 + i) * 2 + inlet]
 };
 
 // Batched ensemble: many independent domains stepped by single launches.
@@ -55,6 +56,9 @@ struct KernelSet {
   cudaError_t (*mlp_pack)(const LaunchCtx&, const float* w, unsigned char* img);
   cudaError_t (*batch_prepare)();
   cudaError_t (*batch_step)(const BatchCtx&, int parity);
+  // The complete equilibria of the two inlet states of the opposed-jets frame:
+  // buf = [out: S * 27 * 2][zero: S * 27][X: M * 2][u: 3 * 2][T: 2][P: 2].
+  cudaError_t (*jet_table)(const LaunchCtx&, double* buf);
   int launches_per_step;
   int setup_launches;                        // kernels of init_fields / set_populations
   int collide_bs;                            // nodes per collide block

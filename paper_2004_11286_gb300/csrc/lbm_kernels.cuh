@@ -17,6 +17,7 @@
 #include "lbm_collide.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_readers.cuh"
+#include "lbm_frame.cuh"
 
 namespace lbm {
 
@@ -266,11 +267,15 @@ struct Launch {
   // holds the stored type (FP64, FP32).
   template <int CL>
   static void collide(const LaunchCtx& c, int parity, Real* side) {
-    // Walls normal to x (bounce-back): register loads, exact closure (the
-    // host refuses walls with the network closure).
+    // Walls normal to x (bounce-back), the opposed-jets frame: register
+    // loads, exact closure (the host refuses both with the network closure).
     if constexpr (CL == 0) {
       if (P(c).wall_x) {
         collide_launch<0, 0, 1>(c, parity, side);
+        return;
+      }
+      if (P(c).frame) {
+        collide_launch<0, 0, 2>(c, parity, side);
         return;
       }
     }
@@ -291,14 +296,24 @@ struct Launch {
     } else {
       collide<0>(c, parity, side);
     }
+    // opposed-jets frame: the populations and side fields of the frame nodes
+    const bool frame = P(c).frame != 0;
+    const unsigned fgrid = frame ? grid_for(frame_count(P(c)), BLOCK_LIGHT) : 0u;
+    if (frame) {
+      frame_pops_kernel<M, Real, Store><<<fgrid, BLOCK_LIGHT, 0, c.stream>>>(P(c), (Store*)c.pops, c.jet, c.base,
+                                                                             parity);
+      frame_side_kernel<Real><<<fgrid, BLOCK_LIGHT, 0, c.stream>>>(P(c), side, 0);
+    }
     if (c.ev) cudaEventRecord(c.ev[1], c.stream);
     // Row-blocked stencils (ROWV nodes per thread) where rows split evenly.
     const bool rows = P(c).nx % ROWV == 0 && !P(c).tvar;
     if (rows) grad_GK_row_kernel<Real><<<grid_for(c.N / ROWV, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     else grad_GK_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
+    if (frame) frame_side_kernel<Real><<<fgrid, BLOCK_LIGHT, 0, c.stream>>>(P(c), side, 1);
     if (c.ev) cudaEventRecord(c.ev[2], c.stream);
     if (rows) grad_X_row_kernel<Real><<<grid_for(c.N / ROWV, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
     else grad_X_kernel<Real><<<grid_for(c.N, BLOCK_LIGHT), BLOCK_LIGHT, 0, c.stream>>>(P(c), side);
+    if (frame) frame_side_kernel<Real><<<fgrid, BLOCK_LIGHT, 0, c.stream>>>(P(c), side, 2);
     if (c.ev) cudaEventRecord(c.ev[3], c.stream);
     return cudaGetLastError();
   }
@@ -367,12 +382,25 @@ struct Launch {
     diag_final_kernel<<<1, DIAG_BLOCK, 0, c.stream>>>(c.partials, (int)nb, M + 5, d_sums);
     return cudaGetLastError();
   }
+  static cudaError_t jet_table(const LaunchCtx& c, double* buf) {
+    DevParams<double> q = *c.p64;
+    q.N = 2; q.nx = 2; q.ny = 1; q.nz = 1; q.wall_x = 0; q.frame = 0;
+    const size_t S = M + 2;
+    double* out = buf;
+    const double* zero = buf + S * Q * 2;
+    const double* X = zero + S * Q;
+    const double* u = X + 2 * M;
+    const double* T = u + 6;
+    const double* Pr = T + 2;
+    init_kernel<M, double><<<1, BLOCK_LIGHT, 0, c.stream>>>(q, *c.p32, out, nullptr, zero, X, u, T, Pr);
+    return cudaGetLastError();
+  }
   static KernelSet make() {
     KernelSet k;
     k.init = &init; k.step = &step; k.moments = &moments; k.get_pops = &get_pops;
     k.set_pops = &set_pops; k.diag = &diag;
     k.samples = &samples; k.mlp_forward = &mlp_forward; k.mlp_pack = &mlp_pack;
-    k.batch_prepare = &batch_prepare; k.batch_step = &batch_step;
+    k.batch_prepare = &batch_prepare; k.batch_step = &batch_step; k.jet_table = &jet_table;
     k.launches_per_step = 3;
     k.setup_launches = EQ ? 2 : 1;
     k.collide_bs = collide_block<M, Real, 0, Store>();
