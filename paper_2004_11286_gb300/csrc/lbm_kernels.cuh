@@ -274,9 +274,11 @@ struct Launch {
         collide_launch<0, 0, 1>(c, parity, side);
         return;
       }
-      if (P(c).frame) {
-        collide_launch<0, 0, 2>(c, parity, side);
-        return;
+      if constexpr (!EQ) {
+        if (P(c).frame) {
+          collide_launch<0, 0, 2>(c, parity, side);
+          return;
+        }
       }
     }
     if constexpr (CL == 0 && LBM_COLLIDE_BULK && M >= LBM_COLLIDE_BULK_MIN_M && std::is_same<Real, Store>::value) {
