@@ -58,8 +58,6 @@ struct DevParams {
   int slaved;            // strong coupling: slaved species index
   int weak;              // 1 = weak coupling (Sec. 3.5.1)
   int wall_x;            // 1 = bounce-back walls at x = -1/2 and x = nx - 1/2 (closed tube)
-  int frame;             // 1 = opposed-jets frame (lbm_frame.cuh): nozzle rows [jet_y0, jet_y1)
-  int jet_y0, jet_y1;
   int omega_is_fixed, omega1_is_fixed;
   Real omega_fixed, omega1_fixed;
   Real R_U;
@@ -101,6 +99,8 @@ struct DevParams {
   int tvar, nterm;
   Real cvp[MAXM][3], Uc[MAXM][3], Hc[MAXM][3], Uar[MAXM];
   Real Ur;
+  int frame;             // 1 = opposed-jets frame (lbm_frame.cuh): nozzle rows [jet_y0, jet_y1)
+  int jet_y0, jet_y1;
 };
 
 // Byte offsets k * N * sizeof(stored type) of the population planes
