@@ -45,17 +45,20 @@ def test_params_struct_layout(tmp_path):
     from paper_2004_11286_gb300.binding import lbm_mix_params
     c = tmp_path / "layout.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm_mix.h"\n'
-                 "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(lbm_mix_params),"
+                 "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lbm_mix_params),"
                  " offsetof(lbm_mix_params, omega_fixed), offsetof(lbm_mix_params, nx),"
                  " offsetof(lbm_mix_params, slaved_species), offsetof(lbm_mix_params, fp64_cond_bound),"
-                 " offsetof(lbm_mix_params, closure_residual_bound));"
+                 " offsetof(lbm_mix_params, closure_residual_bound), offsetof(lbm_mix_params, cv_terms),"
+                 " offsetof(lbm_mix_params, jet_X), offsetof(lbm_mix_params, jet_P),"
+                 " offsetof(lbm_mix_params, jet_y1));"
                  "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     P = lbm_mix_params
     assert vals == [ct.sizeof(P), P.omega_fixed.offset, P.nx.offset, P.slaved_species.offset,
-                    P.fp64_cond_bound.offset, P.closure_residual_bound.offset]
+                    P.fp64_cond_bound.offset, P.closure_residual_bound.offset, P.cv_terms.offset,
+                    P.jet_X.offset, P.jet_P.offset, P.jet_y1.offset]
 
 
 def _params(M=2, **over):
