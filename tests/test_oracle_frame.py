@@ -166,3 +166,23 @@ def test_outlets_let_a_composition_bump_leave():
         b = O.step(b, prm_per)
     assert abs(mass(b) - mass(pops)) < 1e-12 * mass(pops)
     assert mass(a) < mass(pops) * (1.0 - 1e-3)
+
+
+def test_jets_recipe():
+    """The opposed-jets inputs: the printed jet compositions (floored and
+    renormalised), nozzles over [0.1, 0.9] of the height, jets of equal
+    momentum flux rho U^2 at a common T and P, and the framed grid one node
+    larger on every x and y face."""
+    wl, inl = W.opposed_jets()
+    assert wl.shape == (1, 400, 200)
+    assert (inl.y0, inl.y1) == (40, 360)
+    for k in range(2):
+        assert abs(inl.X[k].sum() - 1.0) < 1e-15 and inl.X[k].min() > 0.0098   # floor 0.01, renormalised
+    assert inl.X[0][0] > 0.09 and inl.X[1][2] > 0.09             # H2 left, O2 right, as printed
+    rho = [float(inl.X[k] @ wl.molar_mass) * inl.P[k] / inl.T[k] for k in range(2)]
+    assert inl.u[0] > 0 > inl.u[1]
+    assert abs(rho[0] * inl.u[0] ** 2 - rho[1] * inl.u[1] ** 2) < 1e-12 * rho[0] * inl.u[0] ** 2
+    framed = W.with_frame(wl.X)
+    assert framed.shape == (wl.M, 1, 402, 202)
+    assert np.array_equal(framed[..., 1:-1, 1:-1], wl.X)
+    assert np.array_equal(framed[..., 0, 1:-1], wl.X[..., 0, :])
