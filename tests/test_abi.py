@@ -171,3 +171,21 @@ def test_null_handle_calls_fail_cleanly(built_library):
     assert lib.lbm_mix_step(None, 1) == 1
     assert lib.lbm_mix_destroy(None) == 1
     assert lib.lbm_mix_step_count(None) == -1
+
+
+def test_make_params_jets():
+    """The opposed-jets boundary set through the binding: jet faces on x,
+    outlets on y, z periodic, and the nozzle and inlet fields as given."""
+    import types
+    import numpy as np
+    from paper_2004_11286_gb300 import binding
+    jets = types.SimpleNamespace(y0=3, y1=9, X=np.array([[0.2, 0.8], [0.6, 0.4]]), u=np.array([0.01, -0.02]),
+                                 T=np.array([0.2, 0.3]), P=np.array([0.01, 0.02]))
+    p, keep = binding.make_params([2.0, 28.0], [2.5, 2.5], [[0, 0.05], [0.05, 0]], mu=[0.1, 0.1], lam=[0.1, 0.1],
+                                  shape=(1, 12, 10), jets=jets)
+    assert list(p.bc) == [2, 2, 3, 3, 0, 0]
+    assert (p.jet_y0, p.jet_y1) == (3, 9)
+    assert [p.jet_X[k] for k in range(4)] == [0.2, 0.8, 0.6, 0.4]
+    assert list(p.jet_u) == [0.01, -0.02] and list(p.jet_T) == [0.2, 0.3] and list(p.jet_P) == [0.01, 0.02]
+    p2, _ = binding.make_params([2.0, 28.0], [2.5, 2.5], [[0, 0.05], [0.05, 0]], mu=[0.1, 0.1], lam=[0.1, 0.1])
+    assert list(p2.bc) == [0] * 6 and not p2.jet_X
